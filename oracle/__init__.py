@@ -1,0 +1,21 @@
+"""CPU FP64 oracle of CholeskyQR2 -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, the package's smoke check and the benchmark's CPU-baseline leg may
+import this package; the GPU library neither imports nor links it.
+"""
+from .cholqr2 import (  # noqa: F401
+    NotSPD,
+    PassFailed,
+    back_substitution,
+    cholinv,
+    cqr,
+    cqr2,
+    lstsq,
+    nominal_flops,
+    orthogonality,
+    q_rows,
+    rel_error,
+    residual,
+    syrk,
+)
+from .householder import householder_qr  # noqa: F401

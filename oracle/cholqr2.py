@@ -1,0 +1,218 @@
+"""CPU FP64 oracle of CholeskyQR2 (Hutter & Solomonik, "Communication-avoiding
+CholeskyQR2 for rectangular matrices", arXiv 1710.08471).
+
+TEST INFRASTRUCTURE ONLY. Only the test-suite, the package smoke check and the
+CPU-baseline leg of the benchmark may import this module. The GPU library never
+calls it and shares no code with it.
+
+The oracle follows the paper's algorithms step by step, in the paper's order
+and notation, with numpy FP64 (IEEE round-to-nearest) arithmetic:
+
+* Syrk    (Section II-A):  W = A^T A.
+* CholInv (Algorithm 1, Section II-D): [L, Y] = CholInv(W), W = L L^T, Y = L^-1,
+  by halving recursion down to dimension 1.
+* CQR     (Algorithm CQR, Section II-E): W = Syrk(A); R^T, R^-T = CholInv(W);
+  Q = A R^-1.
+* CQR2    (Algorithm CQR2, Section II-E): (Q1, R1) = CQR(A); (Q, R2) = CQR(Q1);
+  R = R2 R1.
+
+Readings of points the paper leaves open (each also listed in the design notes):
+
+* Split point of an odd dimension: n1 = floor(n/2) (the paper says "n/2").
+* Y21 association: U = L21 Y11 first, then Y21 = -Y22 U, the order of
+  Algorithm CFR3D.
+* Which Syrk triangle: the upper triangle is kept and mirrored, so W is
+  exactly symmetric; CholInv reads only its lower triangle and diagonal.
+* Breakdown: a pivot that is not > 0 (or not finite) raises NotSPD with its
+  index; the paper states accuracy only for kappa(A) = O(eps^-1/2) and gives
+  no recovery.
+* Least squares (the paper names least squares as the use, Section I, but
+  gives no method): x solves R x = Q^T b by back substitution.
+
+Matrix products use numpy's matmul (a library primitive); nothing is blocked,
+fused or reordered beyond what the algorithms state.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+class NotSPD(ArithmeticError):
+    """Cholesky breakdown: pivot `pivot` (0-based, within the CholInv call)
+    was not a finite positive number."""
+
+    def __init__(self, pivot: int, value: float):
+        super().__init__(f"non-positive or non-finite pivot {value!r} at index {pivot}")
+        self.pivot = pivot
+        self.value = value
+
+
+def syrk(A: np.ndarray) -> np.ndarray:
+    """W = A^T A (Syrk, Section II-A; Algorithm CQR step 1).
+
+    The upper triangle is computed by a matmul and mirrored into the lower one.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    W = A.T @ A
+    U = np.triu(W)
+    return U + np.triu(U, 1).T
+
+
+def _cholinv(A: np.ndarray, offset: int) -> tuple[np.ndarray, np.ndarray]:
+    n = A.shape[0]
+    if n == 1:
+        # Base case of Algorithm 1: L = Chol(A) = sqrt(a), Y = L^-1.
+        a = float(A[0, 0])
+        if not (a > 0.0) or not math.isfinite(a):
+            raise NotSPD(offset, a)
+        l = math.sqrt(a)
+        return np.array([[l]]), np.array([[1.0 / l]])
+    n1 = n // 2
+    A11 = A[:n1, :n1]
+    A21 = A[n1:, :n1]
+    A22 = A[n1:, n1:]
+    # Algorithm 1: [L11, Y11] = CholInv(A11)
+    L11, Y11 = _cholinv(A11, offset)
+    # L21 = A21 Y11^T  (= A21 L11^-T)
+    L21 = A21 @ Y11.T
+    # [L22, Y22] = CholInv(A22 - L21 L21^T)
+    L22, Y22 = _cholinv(A22 - L21 @ L21.T, offset + n1)
+    # Y21 = -Y22 L21 Y11, associated as U = L21 Y11, Y21 = -Y22 U (Algorithm CFR3D)
+    U = L21 @ Y11
+    Y21 = -(Y22 @ U)
+    L = np.zeros((n, n))
+    Y = np.zeros((n, n))
+    L[:n1, :n1] = L11
+    L[n1:, :n1] = L21
+    L[n1:, n1:] = L22
+    Y[:n1, :n1] = Y11
+    Y[n1:, :n1] = Y21
+    Y[n1:, n1:] = Y22
+    return L, Y
+
+
+def cholinv(W: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """[L, Y] = CholInv(W) (Algorithm 1, Section II-D).
+
+    W symmetric positive definite n x n. Returns lower-triangular L with
+    W = L L^T and Y = L^-1 (lower triangular). Raises NotSPD on breakdown.
+    """
+    W = np.asarray(W, dtype=np.float64)
+    if W.ndim != 2 or W.shape[0] != W.shape[1] or W.shape[0] < 1:
+        raise ValueError("CholInv needs a non-empty square matrix")
+    return _cholinv(W, 0)
+
+
+def cqr(A: np.ndarray) -> tuple[np.ndarray, np.ndarray, dict]:
+    """[Q, R] = CQR(A) (Algorithm CQR, Section II-E).
+
+    Returns Q, R and the intermediates {W, L, Y, Rinv}. R = L^T is upper
+    triangular and Rinv = Y^T = R^-1; Q = A R^-1.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    W = syrk(A)  # W = Syrk(A)
+    L, Y = cholinv(W)  # R^T, R^-T = CholInv(W)
+    R = np.ascontiguousarray(L.T)
+    Rinv = np.ascontiguousarray(Y.T)
+    Q = A @ Rinv  # Q = MM(A, R^-1)
+    return Q, R, dict(W=W, L=L, Y=Y, Rinv=Rinv)
+
+
+class PassFailed(NotSPD):
+    """NotSPD raised inside pass `pass_no` (1 or 2) of CQR2."""
+
+    def __init__(self, pass_no: int, err: NotSPD):
+        super().__init__(err.pivot, err.value)
+        self.pass_no = pass_no
+
+
+def cqr2(A: np.ndarray, keep: bool = False):
+    """[Q, R] = CQR2(A) (Algorithm CQR2, Section II-E).
+
+    (Q1, R1) = CQR(A); (Q, R2) = CQR(Q1); R = R2 R1. With keep=True also
+    returns a dict of intermediates (pass-1 and pass-2 W, L, Y, Rinv, Q1, R1,
+    R2).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if m < n or n < 1:
+        raise ValueError("CQR2 needs an m x n matrix with m >= n >= 1")
+    try:
+        Q1, R1, i1 = cqr(A)
+    except NotSPD as e:
+        raise PassFailed(1, e) from None
+    try:
+        Q, R2, i2 = cqr(Q1)
+    except NotSPD as e:
+        raise PassFailed(2, e) from None
+    R = np.triu(R2 @ R1)  # R = MM(R2, R1): a product of upper triangles is upper
+    if not keep:
+        return Q, R
+    info = dict(Q1=Q1, R1=R1, R2=R2)
+    for k, v in i1.items():
+        info[k + "1"] = v
+    for k, v in i2.items():
+        info[k + "2"] = v
+    return Q, R, info
+
+
+def back_substitution(R: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Solve R x = c for upper-triangular R, last unknown first."""
+    n = R.shape[0]
+    x = np.array(c, dtype=np.float64, copy=True)
+    for j in range(n - 1, -1, -1):
+        x[j] = x[j] / R[j, j]
+        x[:j] -= R[:j, j] * x[j]
+    return x
+
+
+def lstsq(A: np.ndarray, b: np.ndarray, keep: bool = False):
+    """Least squares min ||A x - b|| through CQR2: x solves R x = Q^T b."""
+    Q, R = cqr2(A)
+    c = Q.T @ np.asarray(b, dtype=np.float64)
+    x = back_substitution(R, c)
+    if keep:
+        return x, Q, R
+    return x
+
+
+def q_rows(A_rows: np.ndarray, Rinv1: np.ndarray, Rinv2: np.ndarray) -> np.ndarray:
+    """Rows of CQR2's Q for selected rows of A: (A_rows R1^-1) R2^-1.
+
+    Q = A R^-1 acts on each row of A independently (Algorithm CQR step 3), so
+    these are exactly the corresponding rows of the full oracle's Q.
+    """
+    return (np.asarray(A_rows, dtype=np.float64) @ Rinv1) @ Rinv2
+
+
+# ---------------------------------------------------------------- error norms
+
+def orthogonality(Q: np.ndarray) -> float:
+    """||Q^T Q - I||_F."""
+    G = Q.T @ Q
+    G[np.diag_indices_from(G)] -= 1.0
+    return float(np.linalg.norm(G))
+
+
+def residual(A: np.ndarray, Q: np.ndarray, R: np.ndarray, block: int = 1 << 18) -> float:
+    """||Q R - A||_F / ||A||_F, accumulated over row blocks."""
+    num = 0.0
+    den = 0.0
+    for r0 in range(0, A.shape[0], block):
+        a = A[r0:r0 + block]
+        d = Q[r0:r0 + block] @ R - a
+        num += float(np.sum(d * d))
+        den += float(np.sum(a * a))
+    return math.sqrt(num) / math.sqrt(den)
+
+
+def rel_error(X: np.ndarray, X_ref: np.ndarray) -> float:
+    """||X - X_ref||_F / ||X_ref||_F."""
+    return float(np.linalg.norm(X - X_ref) / np.linalg.norm(X_ref))
+
+
+def nominal_flops(m: int, n: int) -> float:
+    """Flops of CQR2 as the paper counts them (Section IV): 4 m n^2 + 5 n^3 / 3."""
+    return 4.0 * m * n * n + 5.0 * n ** 3 / 3.0

@@ -1,0 +1,288 @@
+"""Pins of the CPU FP64 oracle against facts that do not come from the oracle.
+
+* exact closed forms for CholInv (min(i,j) and Pascal matrices, golden files);
+* brute force: an independent Householder QR, itself checked against LAPACK;
+* closed forms for CQR2: A = U R0, n = 1, orthonormal A, A = U diag(d);
+* invariants: Q^T Q = I, Q R = A, R upper with positive diagonal, and the
+  kappa^2 law of the first CholeskyQR pass against the O(eps) second pass
+  (Section I);
+* least squares against a consistent system and the normal equations;
+* breakdown reporting;
+* planted mistakes: mutated copies of the oracle must fail these pins.
+"""
+from __future__ import annotations
+
+import inspect
+import math
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.cholqr2 as ocq
+import synth
+from closed_forms import minij, pascal, read_golden, upper_with_kappa
+
+EPS = 2.0 ** -53
+
+
+# ------------------------------------------------------------ CholInv pins
+
+@pytest.mark.parametrize("name,gen", [("minij_n6.txt", minij), ("pascal_n5.txt", pascal)])
+def test_cholinv_golden_fixture(name, gen):
+    g = read_golden(name)
+    n = g["W"].shape[0]
+    W, L, Y = gen(n)
+    np.testing.assert_array_equal(W, g["W"])
+    np.testing.assert_array_equal(L, g["L"])
+    np.testing.assert_array_equal(Y, g["Y"])
+    Lo, Yo = oracle.cholinv(g["W"])
+    np.testing.assert_array_equal(Lo, g["L"])
+    np.testing.assert_array_equal(Yo, g["Y"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8, 13, 64, 100, 129, 257, 512])
+def test_cholinv_minij_exact(n):
+    W, L, Y = minij(n)
+    Lo, Yo = oracle.cholinv(W)
+    np.testing.assert_array_equal(Lo, L)
+    np.testing.assert_array_equal(Yo, Y)
+
+
+@pytest.mark.parametrize("n", [2, 3, 6, 9, 16, 21, 28])
+def test_cholinv_pascal_exact(n):
+    W, L, Y = pascal(n)
+    Lo, Yo = oracle.cholinv(W)
+    np.testing.assert_array_equal(Lo, L)
+    np.testing.assert_array_equal(Yo, Y)
+
+
+def test_cholinv_diagonal():
+    d = np.array([4.0, 9.0, 0.25, 16.0, 1.0])
+    Lo, Yo = oracle.cholinv(np.diag(d))
+    np.testing.assert_array_equal(Lo, np.diag(np.sqrt(d)))
+    np.testing.assert_array_equal(Yo, np.diag(1.0 / np.sqrt(d)))
+
+
+@pytest.mark.parametrize("n", [1, 4, 31, 64, 97])
+def test_cholinv_invariants_random_spd(n):
+    A = synth.make_matrix(4 * n + 8, n, 1e3, seed=5)
+    W = A.T @ A
+    L, Y = oracle.cholinv(W)
+    assert np.array_equal(L, np.tril(L)) and np.array_equal(Y, np.tril(Y))
+    assert np.all(np.diag(L) > 0)
+    assert np.linalg.norm(L @ L.T - W) <= 50 * n * EPS * np.linalg.norm(W)
+    # Y = L^-1: both residuals, bounded by cond(L) * n * eps
+    kl = np.linalg.cond(L)
+    assert np.linalg.norm(L @ Y - np.eye(n)) <= 50 * n * kl * EPS
+    assert np.linalg.norm(Y @ L - np.eye(n)) <= 50 * n * kl * EPS
+    # agrees with LAPACK's Cholesky
+    Lref = np.linalg.cholesky(W)
+    assert np.linalg.norm(L - Lref) <= 50 * n * kl * EPS * np.linalg.norm(Lref)
+
+
+def test_cholinv_breakdown_index():
+    W = np.diag([1.0, 2.0, -1.0, 3.0])
+    with pytest.raises(oracle.NotSPD) as e:
+        oracle.cholinv(W)
+    assert e.value.pivot == 2
+    W = np.diag([1.0, 2.0, 3.0, 0.0, 5.0])
+    with pytest.raises(oracle.NotSPD) as e:
+        oracle.cholinv(W)
+    assert e.value.pivot == 3
+    W = np.eye(3)
+    W[1, 1] = np.nan
+    with pytest.raises(oracle.NotSPD) as e:
+        oracle.cholinv(W)
+    assert e.value.pivot == 1
+
+
+# ------------------------------------------------ Householder (brute force)
+
+@pytest.mark.parametrize("m,n", [(5, 1), (8, 8), (40, 7), (256, 32)])
+def test_householder_matches_lapack(m, n):
+    A = synth.make_matrix(m, n, None, seed=11)
+    Q, R = oracle.householder_qr(A)
+    Ql, Rl = np.linalg.qr(A)
+    d = np.sign(np.diag(Rl))
+    Ql, Rl = Ql * d, d[:, None] * Rl
+    assert np.linalg.norm(R - Rl) <= 1e-13 * np.linalg.norm(Rl)
+    assert np.linalg.norm(Q - Ql) <= 1e-13 * math.sqrt(n)
+    assert np.all(np.diag(R) > 0)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(16, 4, None), (64, 16, 1e2), (256, 32, 1e4), (200, 31, 1e3),
+                                       (32, 32, 10.0)])
+def test_cqr2_matches_householder(m, n, kappa):
+    A = synth.make_matrix(m, n, kappa, seed=3)
+    Q, R = oracle.cqr2(A)
+    Qh, Rh = oracle.householder_qr(A)
+    k = kappa or 10.0
+    tol = 10 * n * k * EPS
+    assert oracle.rel_error(R, Rh) <= tol
+    assert np.linalg.norm(Q - Qh) / math.sqrt(n) <= tol
+
+
+# ------------------------------------------------------- CQR2 closed forms
+
+def test_cqr2_n1():
+    a = synth.make_matrix(1000, 1, None, seed=2)
+    Q, R = oracle.cqr2(a)
+    nrm = np.linalg.norm(a[:, 0])
+    assert abs(R[0, 0] - nrm) <= 4 * EPS * nrm
+    assert np.max(np.abs(Q[:, 0] - a[:, 0] / nrm)) <= 8 * EPS
+
+
+@pytest.mark.parametrize("m,n,kappa", [(300, 20, 10.0), (1000, 50, 1e4), (4096, 64, 1e6)])
+def test_cqr2_recovers_U_R0(m, n, kappa):
+    U = synth.random_orthogonal(m, seed=9)[:, :n]
+    R0 = upper_with_kappa(n, kappa, seed=4)
+    A = U @ R0
+    Q, R = oracle.cqr2(A)
+    kr = np.linalg.cond(R0)
+    assert oracle.rel_error(R, R0) <= 20 * n * kr * EPS
+    assert np.linalg.norm(Q - U) <= 20 * n * kr * EPS
+
+
+def test_cqr2_orthonormal_input_gives_identity():
+    U = synth.random_orthogonal(512, seed=8)[:, :40]
+    Q, R = oracle.cqr2(U)
+    assert np.linalg.norm(R - np.eye(40)) <= 100 * EPS * 40
+    assert np.linalg.norm(Q - U) <= 100 * EPS * 40
+
+
+def test_cqr2_scaled_orthonormal_gives_diag():
+    U = synth.random_orthogonal(256, seed=12)[:, :16]
+    d = np.logspace(2, -2, 16)
+    Q, R = oracle.cqr2(U * d)
+    assert np.linalg.norm(R - np.diag(d)) <= 100 * 16 * 1e4 * EPS * np.linalg.norm(d)
+    assert np.linalg.norm(Q - U) <= 100 * 16 * 1e4 * EPS
+
+
+# ------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("kappa", [None, 1e2, 1e4, 1e6])
+def test_cqr2_invariants(kappa):
+    m, n = 4096, 64
+    A = synth.make_matrix(m, n, kappa, seed=1)
+    Q, R, info = oracle.cqr2(A, keep=True)
+    assert np.array_equal(R, np.triu(R))
+    assert np.all(np.diag(R) > 0)
+    assert oracle.orthogonality(Q) <= 1e-13
+    assert oracle.residual(A, Q, R) <= 1e-14
+    # Section I: CholeskyQR's Q has error Theta(kappa^2 eps); the second pass
+    # factors a nearly orthogonal Q1 so R2 is near identity.
+    k = kappa or 1.3
+    o1 = oracle.orthogonality(info["Q1"])
+    assert o1 <= 10 * n * k * k * EPS
+    assert np.linalg.norm(info["R2"] - np.eye(n)) <= 10 * n * k * k * EPS
+
+
+def test_first_pass_error_grows_as_kappa_squared():
+    m, n = 4096, 32
+    o1 = []
+    for kappa in (1e3, 1e5):
+        A = synth.make_matrix(m, n, kappa, seed=21)
+        _, _, info = oracle.cqr2(A, keep=True)
+        o1.append(oracle.orthogonality(info["Q1"]))
+    ratio = o1[1] / o1[0]
+    # kappa grows 100x, so the first-pass loss of orthogonality grows ~1e4x
+    assert 1e3 <= ratio <= 1e5, ratio
+
+
+def test_cqr2_breakdown_reports_pass():
+    A = synth.make_matrix(100, 6, None, seed=3)
+    A[:, 4] = 0.0
+    with pytest.raises(oracle.PassFailed) as e:
+        oracle.cqr2(A)
+    assert e.value.pass_no == 1 and e.value.pivot == 4
+
+
+def test_cqr2_rejects_wide():
+    with pytest.raises(ValueError):
+        oracle.cqr2(np.ones((3, 5)))
+
+
+# --------------------------------------------------------- least squares
+
+def test_lstsq_consistent_system():
+    A = synth.make_matrix(2000, 48, 1e4, seed=31)
+    x0 = np.linspace(-1, 1, 48)
+    b = A @ x0
+    x = oracle.lstsq(A, b)
+    assert np.linalg.norm(x - x0) <= 100 * 48 * 1e4 * EPS * np.linalg.norm(x0)
+
+
+def test_lstsq_normal_equations():
+    A = synth.make_matrix(3000, 40, 1e3, seed=32)
+    b = synth.make_rhs(3000, seed=32)
+    x = oracle.lstsq(A, b)
+    r = A @ x - b
+    assert np.linalg.norm(A.T @ r) <= 1e-12 * np.linalg.norm(A) * np.linalg.norm(r)
+    xl = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.linalg.norm(x - xl) <= 1e-10 * np.linalg.norm(xl)
+
+
+def test_back_substitution_exact():
+    R = np.array([[2.0, 1.0, -1.0], [0.0, 4.0, 2.0], [0.0, 0.0, 0.5]])
+    x = np.array([1.0, -2.0, 4.0])
+    np.testing.assert_array_equal(oracle.back_substitution(R, R @ x), x)
+
+
+def test_nominal_flops():
+    # Section IV: 4 m n^2 + 5 n^3 / 3
+    assert oracle.nominal_flops(4096, 64) == 4 * 4096 * 64 * 64 + 5 * 64 ** 3 / 3
+
+
+# ------------------------------------------------------ planted mistakes
+
+_MUTATIONS = {
+    "y21_sign": ("Y21 = -(Y22 @ U)", "Y21 = (Y22 @ U)"),
+    "l21_no_transpose": ("L21 = A21 @ Y11.T", "L21 = A21 @ Y11"),
+    "schur_dropped": ("_cholinv(A22 - L21 @ L21.T, offset + n1)", "_cholinv(A22, offset + n1)"),
+    "u_wrong_order": ("U = L21 @ Y11", "U = Y11.T @ L21.T @ Y11.T @ Y11"),
+    "split_index": ("A21 = A[n1:, :n1]", "A21 = A[n1:, :n1].copy(); A21[:, 0] = A[n1:, 1]"),
+    "base_inverse": ("np.array([[1.0 / l]])", "np.array([[1.0 / a]])"),
+    "qform_transposed": ("Q = A @ Rinv", "Q = A @ Rinv.T"),
+    "r_order": ("R = np.triu(R2 @ R1)", "R = np.triu(R1 @ R2)"),
+}
+
+
+def _mutant(key: str) -> types.ModuleType:
+    src = inspect.getsource(ocq)
+    old, new = _MUTATIONS[key]
+    assert src.count(old) == 1, key
+    mod = types.ModuleType(f"oracle_mutant_{key}")
+    exec(compile(src.replace(old, new), f"<mutant {key}>", "exec"), mod.__dict__)
+    return mod
+
+
+def _pins_pass(mod) -> bool:
+    """The core pins, run against a (possibly mutated) oracle module."""
+    try:
+        for n in (6, 9):
+            W, L, Y = pascal(n)
+            Lo, Yo = mod.cholinv(W)
+            if not (np.array_equal(Lo, L) and np.array_equal(Yo, Y)):
+                return False
+        ok = True
+        # kappa 1e6 makes R2 visibly different from I, so R1 R2 != R2 R1
+        for kappa, tol in ((1e2, 1e-12), (1e6, 1e-8)):
+            A = synth.make_matrix(64, 8, kappa, seed=3)
+            Q, R = mod.cqr2(A)
+            Qh, Rh = oracle.householder_qr(A)
+            ok = ok and bool(np.linalg.norm(R - Rh) <= tol * np.linalg.norm(Rh)
+                             and np.linalg.norm(Q - Qh) <= tol)
+        return ok
+    except Exception:
+        return False
+
+
+def test_pins_accept_oracle():
+    assert _pins_pass(ocq)
+
+
+@pytest.mark.parametrize("key", sorted(_MUTATIONS))
+def test_pins_reject_planted_mistake(key):
+    assert not _pins_pass(_mutant(key))
