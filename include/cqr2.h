@@ -1,0 +1,153 @@
+/*
+ * cqr2.h -- C ABI of the GB300 (sm_103a) CholeskyQR2 library.
+ *
+ * CholeskyQR2 (Hutter & Solomonik, "Communication-avoiding CholeskyQR2 for
+ * rectangular matrices", arXiv 1710.08471, Section II-E, Algorithms CQR and
+ * CQR2) computes the reduced QR factorization A = QR of an m x n matrix,
+ * m >= n: Q is m x n with orthonormal columns, R is n x n upper triangular
+ * with a positive diagonal. It runs CholeskyQR twice:
+ *
+ *   pass 1:  W1 = A^T A            (Syrk, Section II-A)
+ *            [L1, Y1] = CholInv(W1) (Algorithm 1, Section II-D), R1 = L1^T
+ *            Q1 = A R1^-1 = A Y1^T
+ *   pass 2:  the same on Q1, giving Q and R2
+ *   finally: R = R2 R1              (Algorithm CQR2, step 3)
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are FP64 and column-major (LAPACK layout): element (i, j) of a
+ *     matrix with leading dimension ld is at ptr[i + j * ld], ld >= rows.
+ *   - Pointers named d* are DEVICE pointers on the current CUDA device; the
+ *     caller owns them and keeps them alive until the stream work completes.
+ *     Host pointers are named h* and may be pageable or pinned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All device work of a plan is enqueued on its stream,
+ *     asynchronously, unless an entry point says it synchronizes.
+ *   - Every step runs in this library's own CUDA kernels. There is no CPU
+ *     fallback: without a usable GPU, plan creation fails with CQR2_ERR_CUDA.
+ *   - No C++ exception crosses this boundary. A plan is not thread-safe; use
+ *     one plan per host thread (plans are independent).
+ *   - Errors: CQR2_ERR_INVALID_ARG for null pointers, m < n, n < 1, or a
+ *     leading dimension smaller than the row count; nothing is enqueued then.
+ *     CQR2_ERR_CUDA when a CUDA call fails. CQR2_ERR_NOT_SPD when a
+ *     Cholesky pivot was not a finite positive number (reported only by calls
+ *     that synchronize, see cqr2_info_t).
+ */
+#ifndef CQR2_H
+#define CQR2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cqr2_plan_st* cqr2_plan_t;
+
+typedef enum {
+  CQR2_OK = 0,
+  CQR2_ERR_INVALID_ARG = 1,
+  CQR2_ERR_NOT_SPD = 2,     /* Cholesky breakdown in pass 1 or 2 */
+  CQR2_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  CQR2_ERR_OOM = 4,         /* device workspace allocation failed */
+  CQR2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  CQR2_ERR_UNSUPPORTED = 6  /* valid request this build does not serve */
+} cqr2_status_t;
+
+/* Arithmetic of the two O(m n^2) contractions (Gram and Q-forming).
+ * CQR2_FP64: native FP64 FMA throughout.
+ * CQR2_OZAKI_BF16: the Gram and Q-forming products are emulated with
+ *   BF16 tensor-core products of error-free slices (Ozaki scheme); CholInv and
+ *   R = R2 R1 stay native FP64. Not part of the paper. */
+typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1 } cqr2_precision_t;
+
+/* Plan flags. */
+#define CQR2_FUSED 0x1u /* fuse pass-1 Q-forming with the pass-2 Gram: Q1 is
+                           produced and its Gram accumulated in one sweep, so
+                           Q1 makes one fewer trip through memory */
+
+/* Device-side outcome of a factorization. */
+typedef struct {
+  int32_t status;       /* CQR2_OK or CQR2_ERR_NOT_SPD */
+  int32_t failed_pass;  /* 0 = none, 1 or 2 = CholeskyQR pass that broke down */
+  int64_t failed_pivot; /* 0-based index of the first bad pivot, -1 = none */
+  double pivot_value;   /* value of that pivot (may be NaN) */
+} cqr2_info_t;
+
+/* Create a plan for m x n factorizations (m >= n >= 1) with the given
+ * precision (cqr2_precision_t) and flags (CQR2_FUSED or 0). Allocates the
+ * device workspace: the split-m partial Gram matrices, W, L, Y and scratch
+ * n x n matrices, and a status word. `stream` may be changed later with
+ * cqr2_plan_set_stream. On failure *plan is set to NULL. */
+cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t precision,
+                               uint32_t flags, void* stream);
+
+/* Bytes of device workspace the plan owns. */
+size_t cqr2_workspace_bytes(cqr2_plan_t plan);
+
+/* Change the stream subsequent calls enqueue on. */
+cqr2_status_t cqr2_plan_set_stream(cqr2_plan_t plan, void* stream);
+
+/* Release the plan and its workspace. Synchronizes the plan's stream first.
+ * NULL is ignored. */
+void cqr2_plan_destroy(cqr2_plan_t plan);
+
+/* CholeskyQR2 (Algorithm CQR2): A = Q R.
+ * dA: m x n input, not modified. dQ: m x n output (may not alias dA).
+ * dR: n x n output, upper triangular with its strictly lower part set to 0.
+ * Q1 is staged in dQ, so the call needs no m x n workspace.
+ * info: if non-NULL, the call synchronizes the stream and fills *info, and
+ * returns CQR2_ERR_NOT_SPD on breakdown; if NULL the call is fully
+ * asynchronous and the outcome can be read later with cqr2_plan_info. */
+cqr2_status_t cqr2_factor(cqr2_plan_t plan, const double* dA, int64_t lda, double* dQ, int64_t ldq,
+                          double* dR, int64_t ldr, cqr2_info_t* info);
+
+/* Least squares min_x ||A x - b||_2 through CholeskyQR2 (the paper names
+ * least squares as the use, Section I; the solve itself is this library's
+ * reading): factor A = QR, c = Q^T b, then x solves R x = c by back
+ * substitution. db: m-vector, dx: n-vector (device). dQ (m x n, ldq) is
+ * required (Q is staged there); dR may be NULL, else receives R. info as in
+ * cqr2_factor. */
+cqr2_status_t cqr2_lstsq(cqr2_plan_t plan, const double* dA, int64_t lda, const double* db, double* dx,
+                         double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info);
+
+/* Synchronize the plan's stream and report the outcome of the last
+ * factorization enqueued on the plan. */
+cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info);
+
+/* ---- Step-level entry points (each one step of Algorithm CQR on the
+ * plan's m x n shape, on the plan's stream, asynchronous). ---- */
+
+/* Syrk (Section II-A, Algorithm CQR step 1): W = A^T A, n x n, both
+ * triangles written (symmetric). dA m x n. */
+cqr2_status_t cqr2_syrk(cqr2_plan_t plan, const double* dA, int64_t lda, double* dW, int64_t ldw);
+
+/* CholInv (Algorithm 1): W = L L^T with L lower triangular, Y = L^-1.
+ * dW n x n symmetric (only its lower triangle and diagonal are read); dL and
+ * dY n x n outputs, strictly upper parts set to 0. info as in cqr2_factor
+ * (failed_pass is reported as 1). */
+cqr2_status_t cqr2_cholinv(cqr2_plan_t plan, const double* dW, int64_t ldw, double* dL, int64_t ldl,
+                           double* dY, int64_t ldy, cqr2_info_t* info);
+
+/* Q-forming multiply (Algorithm CQR step 3): Q = A Rinv with Rinv n x n
+ * upper triangular (its strictly lower part is ignored). dA m x n, dQ m x n
+ * (may not alias dA). */
+cqr2_status_t cqr2_qform(cqr2_plan_t plan, const double* dA, int64_t lda, const double* dRinv,
+                         int64_t ldri, double* dQ, int64_t ldq);
+
+/* R = R2 R1 for n x n upper-triangular R2, R1 (Algorithm CQR2 step 3);
+ * strictly lower part of R set to 0. dR may not alias the inputs. */
+cqr2_status_t cqr2_trmm_upper(cqr2_plan_t plan, const double* dR2, int64_t ld2, const double* dR1,
+                              int64_t ld1, double* dR, int64_t ldr);
+
+/* Human-readable name of a status code (static string). */
+const char* cqr2_status_string(cqr2_status_t status);
+
+/* Library version string, e.g. "cqr2 0.1 sm_103a". */
+const char* cqr2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CQR2_H */

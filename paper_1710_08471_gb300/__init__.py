@@ -1,0 +1,256 @@
+"""GB300-native CholeskyQR2 (Hutter & Solomonik, arXiv 1710.08471).
+
+Thin Python binding of the C ABI in include/cqr2.h. Every function here only
+marshals arguments (device pointers, leading dimensions, the current CUDA
+stream) into libcqr2.so, whose CUDA kernels do all the arithmetic. PyTorch is
+used for device memory and streams only.
+
+Matrices are column-major like the C ABI: an m x n matrix is a torch tensor of
+shape (m, n) with stride (1, ld), ld >= m. ``colmajor`` and ``empty_colmajor``
+make such tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _native as N
+from ._native import (  # noqa: F401
+    CQR2_ERR_CUDA,
+    CQR2_ERR_INVALID_ARG,
+    CQR2_ERR_NOT_SPD,
+    CQR2_ERR_OOM,
+    CQR2_ERR_UNSUPPORTED,
+    CQR2_FP64,
+    CQR2_FUSED,
+    CQR2_OK,
+    CQR2_OZAKI_BF16,
+    CQR2Error,
+    Info,
+)
+
+__all__ = [
+    "Plan", "colmajor", "empty_colmajor", "factor", "lstsq", "cqr2_plan_create", "cqr2_factor", "cqr2_lstsq",
+    "cqr2_syrk", "cqr2_cholinv", "cqr2_qform", "cqr2_trmm_upper", "cqr2_workspace_bytes", "cqr2_plan_destroy",
+    "cqr2_plan_info", "library_path",
+]
+
+
+def library_path() -> str:
+    return N.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def empty_colmajor(m: int, n: int, device=None, dtype=None):
+    """Uninitialised m x n column-major tensor (stride (1, m))."""
+    torch = _torch()
+    return torch.empty((n, m), device=device, dtype=dtype or torch.float64).t()
+
+
+def colmajor(x):
+    """Column-major copy of a 2-D tensor (returned as-is if already so)."""
+    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _mat(x, rows: int, cols: int, name: str):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if tuple(x.shape) != (rows, cols):
+        raise ValueError(f"{name} must be {rows} x {cols}, got {tuple(x.shape)}")
+    if cols > 1 and x.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride (1, ld))")
+    ld = x.stride(1) if cols > 1 else max(rows, 1)
+    return C.c_void_p(x.data_ptr()), ld
+
+
+def _vec(x, n: int, name: str):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if x.numel() != n or (n > 1 and x.stride(-1) != 1) or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous vector of length {n}")
+    return C.c_void_p(x.data_ptr())
+
+
+def _stream_handle(stream=None) -> C.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ----------------------------------------------------------- raw C ABI
+
+def cqr2_plan_create(m: int, n: int, precision: int = CQR2_FP64, flags: int = 0, stream=None) -> C.c_void_p:
+    lib = N.load()
+    h = C.c_void_p()
+    N.check(lib.cqr2_plan_create(C.byref(h), m, n, precision, flags, _stream_handle(stream)), "cqr2_plan_create")
+    return h
+
+
+def cqr2_plan_destroy(plan) -> None:
+    N.load().cqr2_plan_destroy(plan)
+
+
+def cqr2_workspace_bytes(plan) -> int:
+    return int(N.load().cqr2_workspace_bytes(plan))
+
+
+def cqr2_plan_info(plan) -> Info:
+    info = Info()
+    st = N.load().cqr2_plan_info(plan, C.byref(info))
+    if st not in (CQR2_OK, CQR2_ERR_NOT_SPD):
+        N.check(st, "cqr2_plan_info")
+    return info
+
+
+def cqr2_factor(plan, m, n, A, Q, R, sync: bool = True) -> Info | None:
+    a, lda = _mat(A, m, n, "A")
+    q, ldq = _mat(Q, m, n, "Q")
+    r, ldr = _mat(R, n, n, "R")
+    info = Info() if sync else None
+    st = N.load().cqr2_factor(plan, a, lda, q, ldq, r, ldr, C.byref(info) if sync else None)
+    N.check(st, "cqr2_factor", info)
+    return info
+
+
+def cqr2_lstsq(plan, m, n, A, b, x, Q, R=None, sync: bool = True) -> Info | None:
+    a, lda = _mat(A, m, n, "A")
+    q, ldq = _mat(Q, m, n, "Q")
+    if R is not None:
+        r, ldr = _mat(R, n, n, "R")
+    else:
+        r, ldr = None, n
+    info = Info() if sync else None
+    st = N.load().cqr2_lstsq(plan, a, lda, _vec(b, m, "b"), _vec(x, n, "x"), q, ldq, r, ldr,
+                             C.byref(info) if sync else None)
+    N.check(st, "cqr2_lstsq", info)
+    return info
+
+
+def cqr2_syrk(plan, m, n, A, W) -> None:
+    a, lda = _mat(A, m, n, "A")
+    w, ldw = _mat(W, n, n, "W")
+    N.check(N.load().cqr2_syrk(plan, a, lda, w, ldw), "cqr2_syrk")
+
+
+def cqr2_cholinv(plan, n, W, L, Y, sync: bool = True) -> Info | None:
+    w, ldw = _mat(W, n, n, "W")
+    l_, ldl = _mat(L, n, n, "L")
+    y, ldy = _mat(Y, n, n, "Y")
+    info = Info() if sync else None
+    st = N.load().cqr2_cholinv(plan, w, ldw, l_, ldl, y, ldy, C.byref(info) if sync else None)
+    N.check(st, "cqr2_cholinv", info)
+    return info
+
+
+def cqr2_qform(plan, m, n, A, Rinv, Q) -> None:
+    a, lda = _mat(A, m, n, "A")
+    ri, ldri = _mat(Rinv, n, n, "Rinv")
+    q, ldq = _mat(Q, m, n, "Q")
+    N.check(N.load().cqr2_qform(plan, a, lda, ri, ldri, q, ldq), "cqr2_qform")
+
+
+def cqr2_trmm_upper(plan, n, R2, R1, R) -> None:
+    r2, ld2 = _mat(R2, n, n, "R2")
+    r1, ld1 = _mat(R1, n, n, "R1")
+    r, ldr = _mat(R, n, n, "R")
+    N.check(N.load().cqr2_trmm_upper(plan, r2, ld2, r1, ld1, r, ldr), "cqr2_trmm_upper")
+
+
+# ------------------------------------------------------------ helpers
+
+class Plan:
+    """Owns a cqr2 plan for m x n factorizations on the current device."""
+
+    def __init__(self, m: int, n: int, precision: int = CQR2_FP64, fused: bool = False, stream=None):
+        self.m, self.n = int(m), int(n)
+        self.handle = cqr2_plan_create(self.m, self.n, precision, CQR2_FUSED if fused else 0, stream)
+
+    def set_stream(self, stream) -> None:
+        N.check(N.load().cqr2_plan_set_stream(self.handle, _stream_handle(stream)), "cqr2_plan_set_stream")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return cqr2_workspace_bytes(self.handle)
+
+    def factor(self, A, Q=None, R=None, sync: bool = True):
+        if Q is None:
+            Q = empty_colmajor(self.m, self.n, device=A.device)
+        if R is None:
+            R = empty_colmajor(self.n, self.n, device=A.device)
+        info = cqr2_factor(self.handle, self.m, self.n, A, Q, R, sync)
+        return Q, R, info
+
+    def lstsq(self, A, b, Q=None, R=None, x=None, sync: bool = True):
+        torch = _torch()
+        if Q is None:
+            Q = empty_colmajor(self.m, self.n, device=A.device)
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=A.device)
+        info = cqr2_lstsq(self.handle, self.m, self.n, A, b, x, Q, R, sync)
+        return x, info
+
+    def syrk(self, A, W=None):
+        if W is None:
+            W = empty_colmajor(self.n, self.n, device=A.device)
+        cqr2_syrk(self.handle, self.m, self.n, A, W)
+        return W
+
+    def cholinv(self, W, L=None, Y=None, sync: bool = True):
+        if L is None:
+            L = empty_colmajor(self.n, self.n, device=W.device)
+        if Y is None:
+            Y = empty_colmajor(self.n, self.n, device=W.device)
+        info = cqr2_cholinv(self.handle, self.n, W, L, Y, sync)
+        return L, Y, info
+
+    def qform(self, A, Rinv, Q=None):
+        if Q is None:
+            Q = empty_colmajor(self.m, self.n, device=A.device)
+        cqr2_qform(self.handle, self.m, self.n, A, Rinv, Q)
+        return Q
+
+    def trmm_upper(self, R2, R1, R=None):
+        if R is None:
+            R = empty_colmajor(self.n, self.n, device=R1.device)
+        cqr2_trmm_upper(self.handle, self.n, R2, R1, R)
+        return R
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            cqr2_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def factor(A, fused: bool = False):
+    """CholeskyQR2 of a column-major CUDA float64 matrix: returns (Q, R)."""
+    A = colmajor(A)
+    with Plan(A.shape[0], A.shape[1], fused=fused) as p:
+        Q, R, _ = p.factor(A)
+    return Q, R
+
+
+def lstsq(A, b):
+    """Least squares through CholeskyQR2: returns x."""
+    A = colmajor(A)
+    with Plan(A.shape[0], A.shape[1]) as p:
+        x, _ = p.lstsq(A, b.contiguous())
+    return x

@@ -1,0 +1,320 @@
+// C ABI of the CholeskyQR2 library: plans, workspace, and the sequencing of
+// the kernels of Algorithm CQR2 on the caller's stream.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "../../include/cqr2.h"
+#include "kernels.h"
+
+using namespace cqr2;
+
+struct cqr2_plan_st {
+  int64_t m = 0, n = 0;
+  int precision = CQR2_FP64;
+  unsigned flags = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  GramGeom g;
+  bool small = false;  // n <= 256: panel Q-form kernel, Q1 staged in the output Q
+  bool fused = false;  // CQR2_FUSED requested and n small enough to fuse
+  int64_t gemv_nsplit = 0;
+  // device workspace (one allocation)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* partial = nullptr;
+  double* W = nullptr;
+  double* Wk = nullptr;
+  double* L = nullptr;
+  double* Y = nullptr;
+  double* U = nullptr;
+  double* R1 = nullptr;
+  double* Rf = nullptr;  // final R when the caller passes no R
+  double* Rp = nullptr;
+  double* Q1 = nullptr;  // m x n, only when !small
+  double* lspart = nullptr;
+  DevStatus* st = nullptr;
+  DevStatus* h_st = nullptr;  // pinned host copy
+};
+
+namespace {
+
+inline cqr2_status_t cuda_fail(cudaError_t e) { return e == cudaSuccess ? CQR2_OK : CQR2_ERR_CUDA; }
+
+#define TRY(call)                             \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return CQR2_ERR_CUDA; \
+  } while (0)
+
+cqr2_status_t check_device(const cqr2_plan_st* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CQR2_ERR_CUDA;
+  return dev == p->device ? CQR2_OK : CQR2_ERR_INVALID_ARG;
+}
+
+cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
+  TRY(cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, p->stream));
+  TRY(cudaStreamSynchronize(p->stream));
+  info->status = p->h_st->status ? CQR2_ERR_NOT_SPD : CQR2_OK;
+  info->failed_pass = p->h_st->status ? p->h_st->pass : 0;
+  info->failed_pivot = p->h_st->status ? p->h_st->pivot : -1;
+  info->pivot_value = p->h_st->status ? p->h_st->value : 0.0;
+  return info->status == CQR2_OK ? CQR2_OK : CQR2_ERR_NOT_SPD;
+}
+
+// One CholeskyQR pass (Algorithm CQR) on X (m x n): W = X^T X; [L, Y] =
+// CholInv(W); Qout = X Y^T. For the small path Qout may alias X.
+// If `gram_done`, W already holds X^T X.
+cqr2_status_t cqr_pass(cqr2_plan_st* p, const double* X, int64_t ldx, double* Qout, int64_t ldq, int pass,
+                       bool gram_done) {
+  const int n = (int)p->n;
+  cudaStream_t s = p->stream;
+  if (!gram_done) {
+    TRY(gram_partials(X, ldx, p->m, n, p->g, p->partial, s));
+    TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+  }
+  TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s));
+  if (p->small) {
+    TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
+    TRY(qform_small(X, ldx, p->m, n, p->Rp, Qout, ldq, s));
+  } else {
+    TRY(gemm_f64(p->m, n, n, 1.0, X, ldx, p->Y, n, 0.0, Qout, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+  }
+  return CQR2_OK;
+}
+
+cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                          int64_t ldr) {
+  const int n = (int)p->n;
+  cudaStream_t s = p->stream;
+  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  // ---- pass 1: W1 = A^T A, [L1, Y1] = CholInv(W1)
+  TRY(gram_partials(dA, lda, p->m, n, p->g, p->partial, s));
+  TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+  TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
+  TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
+  cqr2_status_t r;
+  if (p->small) {
+    // Q1 = A R1^-1, staged in dQ
+    TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
+    if (p->fused) {
+      // Q1 and the partial Grams of Q1 in one sweep over A
+      TRY(qform_gram_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->g, p->partial, s));
+      TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+      if ((r = cqr_pass(p, dQ, ldq, dQ, ldq, 2, true)) != CQR2_OK) return r;
+    } else {
+      TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, s));
+      if ((r = cqr_pass(p, dQ, ldq, dQ, ldq, 2, false)) != CQR2_OK) return r;
+    }
+  } else {
+    TRY(gemm_f64(p->m, n, n, 1.0, dA, lda, p->Y, n, 0.0, p->Q1, p->m, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    if ((r = cqr_pass(p, p->Q1, p->m, dQ, ldq, 2, false)) != CQR2_OK) return r;
+  }
+  // ---- R = R2 R1 with R2 = L2^T
+  TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
+               GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+  return CQR2_OK;
+}
+
+bool bad_ld(int64_t ld, int64_t rows) { return ld < std::max<int64_t>(1, rows); }
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+const char* cqr2_status_string(cqr2_status_t s) {
+  switch (s) {
+    case CQR2_OK: return "CQR2_OK";
+    case CQR2_ERR_INVALID_ARG: return "CQR2_ERR_INVALID_ARG";
+    case CQR2_ERR_NOT_SPD: return "CQR2_ERR_NOT_SPD";
+    case CQR2_ERR_CUDA: return "CQR2_ERR_CUDA";
+    case CQR2_ERR_OOM: return "CQR2_ERR_OOM";
+    case CQR2_ERR_TIMEOUT: return "CQR2_ERR_TIMEOUT";
+    case CQR2_ERR_UNSUPPORTED: return "CQR2_ERR_UNSUPPORTED";
+  }
+  return "CQR2_ERR_UNKNOWN";
+}
+
+const char* cqr2_version(void) { return "cqr2 0.1 sm_103a"; }
+
+cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t precision, uint32_t flags,
+                               void* stream) {
+  if (!plan) return CQR2_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (n < 1 || m < n || n > 65535) return CQR2_ERR_INVALID_ARG;
+  if (precision != CQR2_FP64) return CQR2_ERR_UNSUPPORTED;
+  if (flags & ~CQR2_FUSED) return CQR2_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CQR2_ERR_CUDA;
+  auto* p = new (std::nothrow) cqr2_plan_st();
+  if (!p) return CQR2_ERR_OOM;
+  p->m = m;
+  p->n = n;
+  p->precision = precision;
+  p->flags = flags;
+  p->device = dev;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->g = gram_geometry(m, (int)n, 0);
+  p->small = qform_group_width((int)n) > 0;
+  p->fused = (flags & CQR2_FUSED) && qform_gram_fusable((int)n);
+  p->gemv_nsplit = gemv_splits(m, (int)n);
+  const size_t nn = (size_t)n * n * sizeof(double);
+  size_t off[16];
+  size_t sz = 0;
+  int k = 0;
+  auto take = [&](size_t bytes) {
+    off[k++] = sz;
+    sz += align_up(bytes);
+  };
+  take(p->g.partial_doubles() * sizeof(double));                     // 0 partial
+  take(nn);                                                          // 1 W
+  take(nn);                                                          // 2 Wk
+  take(nn);                                                          // 3 L
+  take(nn);                                                          // 4 Y
+  take(nn);                                                          // 5 U
+  take(nn);                                                          // 6 R1
+  take(nn);                                                          // 7 Rf
+  take(rpack_doubles((int)n) * sizeof(double));                      // 8 Rp
+  take(p->small ? 0 : (size_t)m * n * sizeof(double));               // 9 Q1
+  take((size_t)p->gemv_nsplit * n * sizeof(double));                 // 10 lspart
+  take(sizeof(DevStatus));                                           // 11 st
+  if (cudaMalloc(&p->ws, sz) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return CQR2_ERR_OOM;
+  }
+  if (cudaMallocHost(&p->h_st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p->ws);
+    delete p;
+    return CQR2_ERR_OOM;
+  }
+  p->ws_bytes = sz;
+  auto at = [&](int i) { return reinterpret_cast<double*>(p->ws + off[i]); };
+  p->partial = at(0);
+  p->W = at(1);
+  p->Wk = at(2);
+  p->L = at(3);
+  p->Y = at(4);
+  p->U = at(5);
+  p->R1 = at(6);
+  p->Rf = at(7);
+  p->Rp = at(8);
+  p->Q1 = p->small ? nullptr : at(9);
+  p->lspart = at(10);
+  p->st = reinterpret_cast<DevStatus*>(p->ws + off[11]);
+  std::memset(p->h_st, 0, sizeof(DevStatus));
+  if (cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream) != cudaSuccess) {
+    cudaFreeHost(p->h_st);
+    cudaFree(p->ws);
+    delete p;
+    return CQR2_ERR_CUDA;
+  }
+  *plan = p;
+  return CQR2_OK;
+}
+
+size_t cqr2_workspace_bytes(cqr2_plan_t plan) { return plan ? plan->ws_bytes : 0; }
+
+cqr2_status_t cqr2_plan_set_stream(cqr2_plan_t plan, void* stream) {
+  if (!plan) return CQR2_ERR_INVALID_ARG;
+  plan->stream = static_cast<cudaStream_t>(stream);
+  return CQR2_OK;
+}
+
+void cqr2_plan_destroy(cqr2_plan_t plan) {
+  if (!plan) return;
+  cudaStreamSynchronize(plan->stream);
+  cudaFree(plan->ws);
+  cudaFreeHost(plan->h_st);
+  delete plan;
+}
+
+cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info) {
+  if (!plan || !info) return CQR2_ERR_INVALID_ARG;
+  return read_info(plan, info);
+}
+
+cqr2_status_t cqr2_factor(cqr2_plan_t p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                          int64_t ldr, cqr2_info_t* info) {
+  if (!p || !dA || !dQ || !dR) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, p->m) || bad_ld(ldq, p->m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
+  if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  if ((r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) return r;
+  if (info) return read_info(p, info);
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_lstsq(cqr2_plan_t p, const double* dA, int64_t lda, const double* db, double* dx, double* dQ,
+                         int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info) {
+  if (!p || !dA || !db || !dx || !dQ) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, p->m) || bad_ld(ldq, p->m)) return CQR2_ERR_INVALID_ARG;
+  if (dR && bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
+  if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  double* R = dR ? dR : p->Rf;
+  const int64_t ldR = dR ? ldr : p->n;
+  if ((r = factor_impl(p, dA, lda, dQ, ldq, R, ldR)) != CQR2_OK) return r;
+  TRY(gemv_t_partials(dQ, ldq, p->m, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
+  TRY(lstsq_solve(p->lspart, p->gemv_nsplit, (int)p->n, R, ldR, dx, p->stream));
+  if (info) return read_info(p, info);
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_syrk(cqr2_plan_t p, const double* dA, int64_t lda, double* dW, int64_t ldw) {
+  if (!p || !dA || !dW || bad_ld(lda, p->m) || bad_ld(ldw, p->n)) return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  TRY(gram_partials(dA, lda, p->m, (int)p->n, p->g, p->partial, p->stream));
+  TRY(gram_reduce(p->partial, p->g, (int)p->n, dW, ldw, p->stream));
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_cholinv(cqr2_plan_t p, const double* dW, int64_t ldw, double* dL, int64_t ldl, double* dY,
+                           int64_t ldy, cqr2_info_t* info) {
+  if (!p || !dW || !dL || !dY || bad_ld(ldw, p->n) || bad_ld(ldl, p->n) || bad_ld(ldy, p->n))
+    return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
+  TRY(cholinv((int)p->n, dW, ldw, dL, ldl, dY, ldy, p->Wk, p->U, p->st, 1, p->stream));
+  if (info) return read_info(p, info);
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_qform(cqr2_plan_t p, const double* dA, int64_t lda, const double* dRinv, int64_t ldri,
+                         double* dQ, int64_t ldq) {
+  if (!p || !dA || !dRinv || !dQ || bad_ld(lda, p->m) || bad_ld(ldri, p->n) || bad_ld(ldq, p->m))
+    return CQR2_ERR_INVALID_ARG;
+  if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  const int n = (int)p->n;
+  if (p->small) {
+    TRY(pack_rinv_from_upper(dRinv, ldri, n, p->Rp, p->stream));
+    TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->stream));
+  } else {
+    TRY(gemm_f64(p->m, n, n, 1.0, dA, lda, dRinv, ldri, 0.0, dQ, ldq, GEMM_B_UPPER | GEMM_BETA0, p->stream));
+  }
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_trmm_upper(cqr2_plan_t p, const double* dR2, int64_t ld2, const double* dR1, int64_t ld1,
+                              double* dR, int64_t ldr) {
+  if (!p || !dR2 || !dR1 || !dR || bad_ld(ld2, p->n) || bad_ld(ld1, p->n) || bad_ld(ldr, p->n))
+    return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  const int n = (int)p->n;
+  TRY(gemm_f64(n, n, n, 1.0, dR2, ld2, dR1, ld1, 0.0, dR, ldr,
+               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, p->stream));
+  return CQR2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// CholInv (Algorithm 1, Section II-D): [L, Y] = CholInv(W) with W = L L^T and
+// Y = L^-1, by the paper's halving recursion
+//     [L11, Y11] = CholInv(W11)
+//     L21 = W21 Y11^T
+//     [L22, Y22] = CholInv(W22 - L21 L21^T)
+//     Y21 = -Y22 (L21 Y11)            (association of Algorithm CFR3D)
+// run as FP64 GEMM launches on one stream. The recursion stops at a base case
+// of at most 64 (the paper's base case is n = 1; CFR3D stops at n_o and
+// factors the block redundantly, which is what the one-CTA base kernel does).
+// The split point is a multiple of 64 near n/2 instead of floor(n/2): the
+// result is the same factorization, rounded in a different order.
+//
+// The base case holds the block in shared memory, runs a right-looking
+// Cholesky and then a right-looking triangular inverse, and reports the first
+// non-positive or non-finite pivot in the device status word (it keeps going
+// with NaNs instead of trapping, so the context stays usable).
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace cqr2 {
+namespace {
+
+constexpr int NB = CHOLINV_BASE;
+constexpr int LD = NB + 1;
+
+__global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__ Wk, int64_t ldk, int nb,
+                                                      double* __restrict__ L, int64_t ldl, double* __restrict__ Y,
+                                                      int64_t ldy, DevStatus* st, int pass, long long off) {
+  extern __shared__ double smem[];
+  double* S = smem;            // S(i, j) = S[j * LD + i], lower part
+  double* T = smem + NB * LD;  // right-looking inverse workspace / result
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  for (int e = t; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    S[j * LD + i] = (i >= j) ? Wk[i + (int64_t)j * ldk] : 0.0;
+    T[j * LD + i] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Right-looking Cholesky.
+  for (int k = 0; k < nb; ++k) {
+    if (t == 0) {
+      const double d = S[k * LD + k];
+      if (!(d > 0.0) || !isfinite(d)) report_pivot(st, pass, off + k, d);
+      S[k * LD + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double l = S[k * LD + k];
+    for (int i = k + 1 + t; i < nb; i += 256) S[k * LD + i] /= l;
+    __syncthreads();
+    for (int j = k + 1 + tx; j < nb; j += 16)
+      for (int i = j + ty; i < nb; i += 16) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
+    __syncthreads();
+  }
+  // Right-looking inverse: solve L Y = I one row of Y at a time.
+  for (int k = 0; k < nb; ++k) {
+    const double lkk = S[k * LD + k];
+    for (int j = t; j <= k; j += 256) T[j * LD + k] /= lkk;
+    __syncthreads();
+    for (int j = tx; j <= k; j += 16)
+      for (int i = k + 1 + ty; i < nb; i += 16) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+    __syncthreads();
+  }
+  for (int e = t; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    if (i >= j) {
+      L[i + (int64_t)j * ldl] = S[j * LD + i];
+      Y[i + (int64_t)j * ldy] = T[j * LD + i];
+    }
+  }
+}
+
+__global__ void k_transpose_lower(const double* __restrict__ L, int64_t ldl, int n, double* __restrict__ R,
+                                  int64_t ldr) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.x * 32, bj = blockIdx.y * 32;  // R block (rows bi.., cols bj..)
+  // read L block (rows bj.., cols bi..) coalesced along its rows
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int li = bj + threadIdx.x, lj = bi + y;
+    tile[y][threadIdx.x] = (li < n && lj < n) ? L[li + (int64_t)lj * ldl] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int ri = bi + threadIdx.x, rj = bj + y;
+    if (ri < n && rj < n) R[ri + (int64_t)rj * ldr] = (ri <= rj) ? tile[threadIdx.x][y] : 0.0;
+  }
+}
+
+__global__ void k_copy_upper(const double* __restrict__ X, int64_t ldx, int n, double* __restrict__ R, int64_t ldr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < n) R[i + (int64_t)j * ldr] = (i <= j) ? X[i + (int64_t)j * ldx] : 0.0;
+}
+
+constexpr size_t BASE_SMEM = 2 * NB * LD * sizeof(double);
+
+cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
+                int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s) {
+  if (n <= NB) {
+    k_cholinv_base<<<1, 256, BASE_SMEM, s>>>(Wk, ldk, n, L, ldl, Y, ldy, st, pass, off);
+    return cudaGetLastError();
+  }
+  const int n1 = NB * (int)ceil_div(n, 2 * NB);
+  const int n2 = n - n1;
+  cudaError_t e;
+  // [L11, Y11] = CholInv(W11)
+  if ((e = rec(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s)) != cudaSuccess) return e;
+  // L21 = W21 Y11^T
+  if ((e = gemm_f64(n2, n1, n1, 1.0, Wk + n1, ldk, Y, ldy, 0.0, L + n1, ldl, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0,
+                    s)) != cudaSuccess)
+    return e;
+  // W22 <- W22 - L21 L21^T (lower triangle)
+  double* W22 = Wk + n1 + (int64_t)n1 * ldk;
+  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s)) !=
+      cudaSuccess)
+    return e;
+  // [L22, Y22] = CholInv(W22 - L21 L21^T)
+  double* L22 = L + n1 + (int64_t)n1 * ldl;
+  double* Y22 = Y + n1 + (int64_t)n1 * ldy;
+  if ((e = rec(n2, W22, ldk, L22, ldl, Y22, ldy, U, ldu, st, pass, off + n1, s)) != cudaSuccess) return e;
+  // U = L21 Y11
+  if ((e = gemm_f64(n2, n1, n1, 1.0, L + n1, ldl, Y, ldy, 0.0, U, ldu, GEMM_B_LOWER | GEMM_BETA0, s)) != cudaSuccess)
+    return e;
+  // Y21 = -Y22 U
+  return gemm_f64(n2, n1, n2, -1.0, Y22, ldy, U, ldu, 0.0, Y + n1, ldy, GEMM_A_LOWER | GEMM_BETA0, s);
+}
+
+}  // namespace
+
+cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
+                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_cholinv_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BASE_SMEM)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpy2DAsync(work, (size_t)n * sizeof(double), W, (size_t)ldw * sizeof(double),
+                             (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemset2DAsync(L, (size_t)ldl * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
+      cudaSuccess)
+    return e;
+  return rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s);
+}
+
+cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int64_t ldr, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32));
+  k_transpose_lower<<<grid, dim3(32, 8), 0, s>>>(L, ldl, n, R, ldr);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_upper(const double* X, int64_t ldx, int n, double* R, int64_t ldr, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(n, 128), (unsigned)n);
+  k_copy_upper<<<grid, 128, 0, s>>>(X, ldx, n, R, ldr);
+  return cudaGetLastError();
+}
+
+}  // namespace cqr2

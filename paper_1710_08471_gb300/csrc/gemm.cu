@@ -1,0 +1,156 @@
+// General FP64 GEMM C = alpha op(A) op(B) + beta C (the MM of Section II-A)
+// with triangular-structure flags, used for the CholInv recursion
+// (Algorithm 1), R = R2 R1, and the Q-forming multiply when n > 256.
+//
+// 64 x 64 x 16 tiles, 256 threads, 4 x 4 register micro-tiles, register
+// double buffering of the next k-slice. GB300's FP64 pipe (about 2 FMA per
+// clock per SM) is the bound, so the structure flags matter more than the
+// load path: a tile's k range is clipped to the blocks that the triangles of
+// op(A) and op(B) leave nonzero, output tiles outside the requested triangle
+// are skipped, and elements inside the zero triangle are never read (they are
+// masked to zero at load), so callers may leave garbage there.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace cqr2 {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha,
+                                                 const double* __restrict__ A, int64_t lda,
+                                                 const double* __restrict__ B, int64_t ldb, double beta,
+                                                 double* __restrict__ C, int64_t ldc, unsigned flags) {
+  __shared__ double As[2][BK][BM + 1];
+  __shared__ double Bs[2][BK][BN + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+
+  if ((flags & GEMM_C_LOWER) && j0 > i0 + BM - 1) return;
+  if ((flags & GEMM_C_UPPER) && i0 > j0 + BN - 1) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t gi = i0 + tx + 16 * r, gj = j0 + ty + 16 * c;
+        if (gi < M && gj < N) C[gi + gj * ldc] = 0.0;
+      }
+    return;
+  }
+  int64_t kb = 0, ke = K;
+  if (flags & GEMM_A_LOWER) ke = min(ke, i0 + BM);
+  if (flags & GEMM_A_UPPER) kb = max(kb, i0);
+  if (flags & GEMM_B_LOWER) kb = max(kb, j0);
+  if (flags & GEMM_B_UPPER) ke = min(ke, j0 + BN);
+  kb = (kb / BK) * BK;
+
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+  double ra[4], rb[4];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * NT;
+      int i, k;
+      if (!TA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
+      const int64_t gi = i0 + i, gk = k0 + k;
+      bool ok = gi < M && gk < K;
+      if (flags & GEMM_A_LOWER) ok = ok && gk <= gi;
+      if (flags & GEMM_A_UPPER) ok = ok && gk >= gi;
+      ra[q] = ok ? (TA ? A[gk + gi * lda] : A[gi + gk * lda]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * NT;
+      int j, k;
+      if (!TB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
+      const int64_t gj = j0 + j, gk = k0 + k;
+      bool ok = gj < N && gk < K;
+      if (flags & GEMM_B_LOWER) ok = ok && gk >= gj;
+      if (flags & GEMM_B_UPPER) ok = ok && gk <= gj;
+      rb[q] = ok ? (TB ? B[gj + gk * ldb] : B[gk + gj * ldb]) : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * NT;
+      int i, k;
+      if (!TA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
+      As[buf][k][i] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * NT;
+      int j, k;
+      if (!TB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
+      Bs[buf][k][j] = rb[q];
+    }
+  };
+
+  if (kb < ke) {
+    load(kb);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+      const bool more = k0 + BK < ke;
+      if (more) load(k0 + BK);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[buf][k][tx + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = Bs[buf][k][ty + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+      }
+      if (more) store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t gi = i0 + tx + 16 * r, gj = j0 + ty + 16 * c;
+      if (gi >= M || gj >= N) continue;
+      if ((flags & GEMM_C_LOWER) && gi < gj) continue;
+      if ((flags & GEMM_C_UPPER) && gi > gj) {
+        C[gi + gj * ldc] = 0.0;
+        continue;
+      }
+      double v = alpha * acc[r][c];
+      if (!(flags & GEMM_BETA0)) v = fma(beta, C[gi + gj * ldc], v);
+      C[gi + gj * ldc] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+                     int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int64_t gx = ceil_div(M, BM), gy = ceil_div(N, BN);
+  if (gy > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  const bool ta = flags & GEMM_TA, tb = flags & GEMM_TB;
+  if (!ta && !tb) k_gemm_f64<false, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  else if (!ta && tb) k_gemm_f64<false, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  else if (ta && !tb) k_gemm_f64<true, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  else k_gemm_f64<true, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace cqr2

@@ -1,0 +1,85 @@
+// Host-side launchers of the CholeskyQR2 kernels (internal, not the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cqr2 {
+
+// ---------------------------------------------------------------- Gram
+// Split-m Syrk W = A^T A (Section II-A; the tall dimension is cut into row
+// ranges whose partial Grams are summed in a fixed order, the single-GPU form
+// of the 1D algorithm's Allreduce, Algorithm 1D-CQR).
+struct GramGeom {
+  int T = 0;              // output tile width (32, 64 or 128)
+  int ntile = 0;          // tiles per side
+  int ntiles_total = 0;   // ntile diagonal + ntile(ntile-1)/2 off-diagonal
+  int64_t nsplit = 0;     // row ranges
+  int64_t rows_per_split = 0;
+  size_t partial_doubles() const { return (size_t)nsplit * ntiles_total * T * T; }
+};
+GramGeom gram_geometry(int64_t m, int n, int64_t max_splits);
+cudaError_t gram_partials(const double* A, int64_t lda, int64_t m, int n, const GramGeom& g,
+                          double* partial, cudaStream_t s);
+cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double* W, int64_t ldw,
+                        cudaStream_t s);
+
+// ---------------------------------------------------------------- Q-form
+// Q = A Rinv for upper-triangular Rinv (Algorithm CQR step 3).
+// Small-n path (n <= 256): one row per lane, warps own column groups.
+int qform_group_width(int n);  // columns per group (16 groups), 0 if n > 256
+size_t rpack_doubles(int n);
+// Rp[g][k][c] = Rinv(k, g*w + c) for k <= g*w + c, else 0; Rinv = Y^T.
+cudaError_t pack_rinv_from_lower(const double* Y, int64_t ldy, int n, double* Rp, cudaStream_t s);
+// Same from an upper-triangular Rinv (strictly lower part ignored).
+cudaError_t pack_rinv_from_upper(const double* Rinv, int64_t ld, int n, double* Rp, cudaStream_t s);
+// Q may alias A (each CTA reads its whole row panel before writing it).
+cudaError_t qform_small(const double* A, int64_t lda, int64_t m, int n, const double* Rp, double* Q,
+                        int64_t ldq, cudaStream_t s);
+// Fused: Q = A Rinv and the partial Grams of Q (same layout as gram_partials
+// with geometry g, which must have T >= n, i.e. one diagonal tile).
+bool qform_gram_fusable(int n);
+cudaError_t qform_gram_small(const double* A, int64_t lda, int64_t m, int n, const double* Rp, double* Q,
+                             int64_t ldq, const GramGeom& g, double* partial, cudaStream_t s);
+
+// ---------------------------------------------------------------- GEMM
+// C = alpha op(A) op(B) + beta C, FP64, column-major. Structure flags let
+// tiles skip blocks that are zero by triangularity.
+enum : unsigned {
+  GEMM_TA = 1u << 0,        // op(A) = A^T
+  GEMM_TB = 1u << 1,        // op(B) = B^T
+  GEMM_A_LOWER = 1u << 2,   // op(A)(i,k) = 0 for k > i
+  GEMM_A_UPPER = 1u << 3,   // op(A)(i,k) = 0 for k < i
+  GEMM_B_LOWER = 1u << 4,   // op(B)(k,j) = 0 for k < j
+  GEMM_B_UPPER = 1u << 5,   // op(B)(k,j) = 0 for k > j
+  GEMM_C_LOWER = 1u << 6,   // only C(i,j), i >= j, is computed and written
+  GEMM_C_UPPER = 1u << 7,   // only C(i,j), i <= j, is computed; i > j written as 0
+  GEMM_BETA0 = 1u << 8,     // C is not read (beta = 0)
+};
+cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- CholInv
+// [L, Y] = CholInv(W) (Algorithm 1): recursive halving with FP64 GEMMs and a
+// one-CTA base case of size <= 64. `work` and `U` are n x n scratch (ld n).
+constexpr int CHOLINV_BASE = 64;
+cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
+                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s);
+// R = L^T (upper) with zeros below the diagonal.
+cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int64_t ldr, cudaStream_t s);
+// R = upper part of X with zeros below the diagonal.
+cudaError_t copy_upper(const double* X, int64_t ldx, int n, double* R, int64_t ldr, cudaStream_t s);
+
+// ---------------------------------------------------------------- lstsq
+// c = Q^T b as split-m partials, then x solves R x = c (back substitution).
+int64_t gemv_splits(int64_t m, int n);
+cudaError_t gemv_t_partials(const double* Q, int64_t ldq, int64_t m, int n, const double* b, int64_t nsplit,
+                            double* partial, cudaStream_t s);
+cudaError_t lstsq_solve(const double* partial, int64_t nsplit, int n, const double* R, int64_t ldr, double* x,
+                        cudaStream_t s);
+
+}  // namespace cqr2
