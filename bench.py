@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of GB300 CholeskyQR2 (Hutter & Solomonik, arXiv 1710.08471).
+
+Default workload (one step = one CholeskyQR2 factorization, Algorithm CQR2):
+FP64 A = G diag(sigma) V with m = 2^23, n = 128, sigma log-spaced 1 .. 1e-6
+(kappa ~ 1e6), fused pass-1 Q-form / pass-2 Gram. The metric is TFLOP/s at
+the paper's nominal 4 m n^2 + 5 n^3 / 3 flops (Section IV), with the roofline
+fraction of the dominant kernel and the three error norms against the CPU
+FP64 oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tall|small|square|wide512] [--variant fused|plain]
+
+Timing: inputs (8.6 GB) are larger than L2 (129 MB), so L2 is not flushed.
+Device time comes from CUDA events on the plan's stream; the end-to-end
+number goes through the host-buffer C entry point with pinned buffers. With
+N > 1 (torchrun) each rank factors its own matrix (replicas, weak scaling);
+the timed region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (m, n, kappa, seed, description)
+    "tall": (1 << 23, 128, 1e6, 1, "FP64 CholeskyQR2, m=2^23 n=128 (8.6 GB), A=G diag(sigma) V, kappa=1e6"),
+    "small": (4096, 64, None, 0, "FP64 CholeskyQR2, m=4096 n=64, iid N(0,1), kappa~1.3"),
+    "square": (65536, 8192, 1e4, 2, "FP64 CholeskyQR2, m=65536 n=8192 (4.3 GB), kappa=1e4"),
+    "wide512": (1 << 21, 512, 1e6, 3, "FP64 CholeskyQR2, m=2^21 n=512 (8.6 GB), kappa=1e6"),
+}
+
+# GB300 FP64: 2 DFMA per clock per SM (one warp instruction every 16 clocks
+# per SM partition), 152 SMs, 2 flops per FMA, at the maximum SM clock.
+FP64_FMA_PER_CLK_PER_SM = 2
+GB300_SMS = 152
+
+# ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by
+# kernel name, workload and the SHA-256 of the source file it was measured
+# from; used only while that source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def nominal_flops(m: int, n: int) -> float:
+    return 4.0 * m * n * n + 5.0 * n ** 3 / 3.0
+
+
+def src_sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_1710_08471_gb300", "csrc", name)
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ helpers
+
+def make_input(m: int, n: int, kappa, seed: int, pinned: bool):
+    import torch
+
+    if pinned:
+        t = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+        A = t.numpy().T  # Fortran-ordered (m, n) view of pinned memory
+    else:
+        t = None
+        A = np.empty((m, n), dtype=np.float64, order="F")
+    synth.make_matrix(m, n, kappa, seed, out=A)
+    return A, t
+
+
+def pinned_colmajor(m: int, n: int):
+    import torch
+
+    t = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+    return t.numpy().T, t
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def allreduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_cores() -> int:
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(A_full: np.ndarray, budget_rows: int):
+    """Time the CPU oracle on the first `budget_rows` rows of the workload."""
+    import oracle
+
+    ms = min(A_full.shape[0], budget_rows)
+    As = np.asfortranarray(A_full[:ms]) if ms < A_full.shape[0] else A_full
+    t0 = time.perf_counter()
+    Q, R = oracle.cqr2(As)
+    dt = time.perf_counter() - t0
+    return ms, dt, Q, R
+
+
+# ------------------------------------------------------------- arms
+
+def bench_reference(args, ws, rank):
+    """The CPU FP64 oracle on the host cores (the reference arm)."""
+    m, n, kappa, seed, desc = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    rows = min(m, args.oracle_rows or (1 << 21))
+    A, _ = make_input(rows, n, kappa, seed, pinned=False)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        import oracle
+
+        oracle.cqr2(A)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    fl = nominal_flops(rows, n)
+    val = fl / (ms * 1e-3) / 1e12
+    sample = f"first {rows} of {m} rows of the workload ({desc}); numpy FP64 oracle"
+    line = {
+        "impl": "reference", "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": val, "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "m": rows, "n": n, "kappa": kappa, "sampled_rows": rows},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args, ws, rank, local):
+    import torch
+
+    import paper_1710_08471_gb300 as cq
+
+    m, n, kappa, seed, desc = WORKLOADS[args.workload]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fused = args.variant == "fused"
+    # inputs: generated on the host (seed + rank), kept pinned for the e2e leg
+    hA, hA_t = make_input(m, n, kappa, seed + 1000 * rank, pinned=True)
+    A = cq.empty_colmajor(m, n, device=dev)
+    A.t().copy_(hA_t.to(dev, non_blocking=True))
+    Q = cq.empty_colmajor(m, n, device=dev)
+    R = cq.empty_colmajor(n, n, device=dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    plan = cq.Plan(m, n, fused=fused, stream=stream)
+    info = plan.factor(A, Q, R, sync=True)[2]
+    if info.status != 0:
+        raise SystemExit(f"factorization failed: {info.status}")
+
+    def timed(pl, steps, warmup, profile):
+        for _ in range(warmup):
+            pl.factor(A, Q, R, sync=False)
+        torch.cuda.synchronize()
+        barrier(ws)
+        pl.set_profiling(profile)
+        l0 = cq.cqr2_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            pl.factor(A, Q, R, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = cq.cqr2_launch_count() - l0
+        barrier(ws)
+        ms = e0.elapsed_time(e1) / steps
+        st = pl.stage_times() if profile else None
+        pl.set_profiling(False)
+        return ms, launches, st
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_local, launches, stages = timed(plan, args.steps, args.warmup, True)
+    clk = clocks.stop()
+    ms_step = allreduce_max(ms_local, ws)
+    flops = nominal_flops(m, n)
+    value = ws * flops / (ms_step * 1e-3) / 1e12
+
+    # dominant stage -> roofline (FP64 ALU bound)
+    per_stage = {k: v[0] / v[1] for k, v in stages.items() if v[1] > 0}
+    dom = max(per_stage, key=per_stage.get)
+    tri = m * n * (n + 1)  # flops of one Syrk or one triangular Q-form (FMA = 2 flops)
+    stage_flops = {"gram1": tri, "qform1": 2 * tri if fused else tri, "gram2": 0 if fused else tri,
+                   "qform2": tri, "cholinv1": 2 * n ** 3 / 3, "cholinv2": 2 * n ** 3 / 3, "trmm": n ** 3 / 3}
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
+    achieved = stage_flops.get(dom, 0) / (per_stage[dom] * 1e-3) / 1e12
+    kern = {"qform1": "k_qform_gram_small" if fused else "k_qform_small", "gram1": "k_gram_tile",
+            "gram2": "k_gram_tile", "qform2": "k_qform_small"}.get(dom, dom)
+    kfile = "qform.cu" if "qform" in kern else "gram.cu"
+    traffic = NCU_TRAFFIC.get(f"{kern}@{args.workload}@{src_sha(kfile)}")
+    roofline = {"bound": "alu", "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_note": f"FP64 DFMA: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 flops x {sm_max:.0f} MHz"}
+    whole = {"achieved": value / ws, "frac": value / ws / peak}
+
+    out = {
+        "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "m": m, "n": n, "kappa": kappa, "variant": args.variant,
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "whole_step_vs_fp64_peak": whole,
+        "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.quick:
+        # the other variant at the same size, for context
+        other = cq.Plan(m, n, fused=not fused, stream=stream)
+        ms_o, _, st_o = timed(other, max(2, args.steps // 2), 1, True)
+        out["variants"] = {("plain" if fused else "fused"): {
+            "ms_per_step": ms_o, "tflops": flops / (ms_o * 1e-3) / 1e12,
+            "stages_ms": {k: round(v[0] / v[1], 4) for k, v in st_o.items() if v[1] > 0}}}
+        other.close()
+        # end to end through the host-buffer C entry point
+        hQ, hQ_t = pinned_colmajor(m, n)
+        hR, hR_t = pinned_colmajor(n, n)
+        plan.factor_host(hA, hQ, hR)  # allocates staging
+        times = []
+        l0 = cq.cqr2_launch_count()
+        for _ in range(max(2, args.steps // 2)):
+            t0 = time.perf_counter()
+            plan.factor_host(hA, hQ, hR)
+            times.append(time.perf_counter() - t0)
+        e2e_ms = 1e3 * statistics.median(times)
+        out["e2e"] = {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                      "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8,
+                      "api": "cqr2_factor_host (pinned host buffers)"}
+        # errors against the CPU FP64 oracle and the oracle's own time
+        Qh = hQ
+        Rh = np.asfortranarray(hR)
+        rows, dt, Qo, Ro = run_oracle_sample(hA, args.oracle_rows or m)
+        import oracle
+
+        err = {"orthogonality": oracle.orthogonality(Qh), "residual": oracle.residual(hA, Qh, Rh)}
+        if rows == m:
+            err["R_rel_vs_oracle"] = oracle.rel_error(Rh, Ro)
+            err["oracle_orthogonality"] = oracle.orthogonality(Qo)
+            err["oracle_residual"] = oracle.residual(hA, Qo, Ro)
+        out["errors"] = err
+        sample = (f"full workload ({desc})" if rows == m else f"first {rows} of {m} rows of the workload ({desc})")
+        out["cpu_baseline"] = {"value": nominal_flops(rows, n) / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+                               "kind": "oracle", "sample": sample + "; numpy FP64 oracle, one run",
+                               "seconds": dt}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tall")
+    ap.add_argument("--variant", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--oracle-rows", type=int, default=None,
+                    help="rows of the workload the CPU oracle runs on (default: all for the error check, "
+                         "2^21 for --impl reference)")
+    ap.add_argument("--quick", action="store_true", help="device timing only (no e2e / oracle legs)")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if ws > 1 and rank != 0:
+            return
+        bench_reference(args, ws, rank)
+        return
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        bench_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

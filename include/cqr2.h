@@ -140,6 +140,52 @@ cqr2_status_t cqr2_qform(cqr2_plan_t plan, const double* dA, int64_t lda, const 
 cqr2_status_t cqr2_trmm_upper(cqr2_plan_t plan, const double* dR2, int64_t ld2, const double* dR1,
                               int64_t ld1, double* dR, int64_t ldr);
 
+/* ---- Host-buffer entry point ---- */
+
+/* CholeskyQR2 of a matrix in HOST memory: copies hA (m x n, lda) to the
+ * device, factors it exactly as cqr2_factor, and copies Q (m x n, ldq) and R
+ * (n x n, ldr) back. Pinned host buffers give full copy bandwidth; pageable
+ * ones work too. The first call allocates device staging for A, Q and R
+ * (2 m n + n^2 doubles) that the plan keeps until it is destroyed. Always
+ * synchronizes; returns CQR2_ERR_NOT_SPD on breakdown (info may be NULL). */
+cqr2_status_t cqr2_factor_host(cqr2_plan_t plan, const double* hA, int64_t lda, double* hQ, int64_t ldq,
+                               double* hR, int64_t ldr, cqr2_info_t* info);
+
+/* ---- Measurement ---- */
+
+/* Stages of a factorization timed by the per-plan profiler. With
+ * CQR2_FUSED, CQR2_STAGE_QFORM1 also accumulates pass 2's partial Grams and
+ * CQR2_STAGE_GRAM2 only sums them. */
+typedef enum {
+  CQR2_STAGE_GRAM1 = 0,
+  CQR2_STAGE_CHOLINV1 = 1,
+  CQR2_STAGE_QFORM1 = 2,
+  CQR2_STAGE_GRAM2 = 3,
+  CQR2_STAGE_CHOLINV2 = 4,
+  CQR2_STAGE_QFORM2 = 5,
+  CQR2_STAGE_TRMM = 6,
+  CQR2_STAGE_LSTSQ = 7,
+  CQR2_STAGE_H2D = 8,
+  CQR2_STAGE_D2H = 9,
+  CQR2_NUM_STAGES = 10
+} cqr2_stage_t;
+
+/* Turn per-stage timing on (1) or off (0) and clear what was recorded. While
+ * on, every stage of every call records a CUDA event before and after it on
+ * the plan's stream (at most 8192 stage records are kept). Synchronizes. */
+cqr2_status_t cqr2_plan_set_profiling(cqr2_plan_t plan, int32_t enable);
+
+/* Synchronize the stream and write, for stages 0..nstages-1, the total
+ * milliseconds recorded since profiling was enabled into ms[] and the
+ * number of timed instances into count[] (count may be NULL). */
+cqr2_status_t cqr2_plan_stage_times(cqr2_plan_t plan, double* ms, int64_t* count, int32_t nstages);
+
+/* Static name of a stage ("gram1", "qform2", ...). */
+const char* cqr2_stage_name(int32_t stage);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t cqr2_launch_count(void);
+
 /* Human-readable name of a status code (static string). */
 const char* cqr2_status_string(cqr2_status_t status);
 

@@ -31,7 +31,8 @@ from ._native import (  # noqa: F401
 __all__ = [
     "Plan", "colmajor", "empty_colmajor", "factor", "lstsq", "cqr2_plan_create", "cqr2_factor", "cqr2_lstsq",
     "cqr2_syrk", "cqr2_cholinv", "cqr2_qform", "cqr2_trmm_upper", "cqr2_workspace_bytes", "cqr2_plan_destroy",
-    "cqr2_plan_info", "library_path",
+    "cqr2_plan_info", "library_path", "cqr2_factor_host", "cqr2_plan_set_profiling", "cqr2_plan_stage_times",
+    "cqr2_launch_count",
 ]
 
 
@@ -163,6 +164,39 @@ def cqr2_trmm_upper(plan, n, R2, R1, R) -> None:
     N.check(N.load().cqr2_trmm_upper(plan, r2, ld2, r1, ld1, r, ldr), "cqr2_trmm_upper")
 
 
+def cqr2_factor_host(plan, m, n, hA, hQ, hR) -> Info:
+    """Host-buffer CholeskyQR2. hA, hQ, hR are Fortran-ordered float64 numpy
+    arrays (pinned or pageable) of shapes (m, n), (m, n), (n, n)."""
+    import numpy as np
+
+    for name, x, shape in (("A", hA, (m, n)), ("Q", hQ, (m, n)), ("R", hR, (n, n))):
+        if not isinstance(x, np.ndarray) or x.dtype != np.float64 or x.shape != shape:
+            raise TypeError(f"{name} must be a float64 numpy array of shape {shape}")
+        if not x.flags.f_contiguous:
+            raise ValueError(f"{name} must be column-major (Fortran order)")
+    info = Info()
+    st = N.load().cqr2_factor_host(plan, hA.ctypes.data, m, hQ.ctypes.data, m, hR.ctypes.data, n, C.byref(info))
+    N.check(st, "cqr2_factor_host", info)
+    return info
+
+
+def cqr2_plan_set_profiling(plan, enable: bool) -> None:
+    N.check(N.load().cqr2_plan_set_profiling(plan, 1 if enable else 0), "cqr2_plan_set_profiling")
+
+
+def cqr2_plan_stage_times(plan) -> dict:
+    """{stage name: (total ms, count)} since profiling was enabled."""
+    lib = N.load()
+    ms = (C.c_double * N.CQR2_NUM_STAGES)()
+    cnt = (C.c_int64 * N.CQR2_NUM_STAGES)()
+    N.check(lib.cqr2_plan_stage_times(plan, ms, cnt, N.CQR2_NUM_STAGES), "cqr2_plan_stage_times")
+    return {lib.cqr2_stage_name(i).decode(): (ms[i], int(cnt[i])) for i in range(N.CQR2_NUM_STAGES)}
+
+
+def cqr2_launch_count() -> int:
+    return int(N.load().cqr2_launch_count())
+
+
 # ------------------------------------------------------------ helpers
 
 class Plan:
@@ -221,6 +255,15 @@ class Plan:
             R = empty_colmajor(self.n, self.n, device=R1.device)
         cqr2_trmm_upper(self.handle, self.n, R2, R1, R)
         return R
+
+    def factor_host(self, hA, hQ, hR) -> Info:
+        return cqr2_factor_host(self.handle, self.m, self.n, hA, hQ, hR)
+
+    def set_profiling(self, enable: bool) -> None:
+        cqr2_plan_set_profiling(self.handle, enable)
+
+    def stage_times(self) -> dict:
+        return cqr2_plan_stage_times(self.handle)
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -22,6 +22,7 @@ CQR2_ERR_UNSUPPORTED = 6
 CQR2_FP64 = 0
 CQR2_OZAKI_BF16 = 1
 CQR2_FUSED = 0x1
+CQR2_NUM_STAGES = 10
 
 
 class Info(C.Structure):
@@ -47,6 +48,11 @@ SIGNATURES = {
     "cqr2_cholinv": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_qform": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64]),
     "cqr2_trmm_upper": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64]),
+    "cqr2_factor_host": (C.c_int, [_P, _P, _I64, _P, _I64, _P, _I64, C.POINTER(Info)]),
+    "cqr2_plan_set_profiling": (C.c_int, [_P, C.c_int32]),
+    "cqr2_plan_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "cqr2_stage_name": (C.c_char_p, [C.c_int32]),
+    "cqr2_launch_count": (C.c_int64, []),
     "cqr2_status_string": (C.c_char_p, [C.c_int]),
     "cqr2_version": (C.c_char_p, []),
 }

@@ -1,13 +1,21 @@
 // C ABI of the CholeskyQR2 library: plans, workspace, and the sequencing of
 // the kernels of Algorithm CQR2 on the caller's stream.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/cqr2.h"
 #include "kernels.h"
 
 using namespace cqr2;
+
+namespace cqr2 {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace cqr2
 
 struct cqr2_plan_st {
   int64_t m = 0, n = 0;
@@ -35,11 +43,18 @@ struct cqr2_plan_st {
   double* lspart = nullptr;
   DevStatus* st = nullptr;
   DevStatus* h_st = nullptr;  // pinned host copy
+  // device staging for cqr2_factor_host (allocated on its first call)
+  double* hA_dev = nullptr;
+  double* hQ_dev = nullptr;
+  double* hR_dev = nullptr;
+  // per-stage CUDA-event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
 };
 
 namespace {
-
-inline cqr2_status_t cuda_fail(cudaError_t e) { return e == cudaSuccess ? CQR2_OK : CQR2_ERR_CUDA; }
 
 #define TRY(call)                             \
   do {                                        \
@@ -53,6 +68,37 @@ cqr2_status_t check_device(const cqr2_plan_st* p) {
   return dev == p->device ? CQR2_OK : CQR2_ERR_INVALID_ARG;
 }
 
+constexpr size_t MAX_MARKS = 8192;
+
+cudaEvent_t take_event(cqr2_plan_st* p) {
+  if (p->ev_used == p->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->ev_pool.push_back(e);
+  }
+  return p->ev_pool[p->ev_used++];
+}
+
+// Records CUDA events on the plan's stream around one stage when profiling.
+struct Stage {
+  cqr2_plan_st* p;
+  int id;
+  cudaEvent_t a = nullptr;
+  Stage(cqr2_plan_st* p_, int id_) : p(p_), id(id_) {
+    if (p->profiling && p->ev_marks.size() < MAX_MARKS) {
+      a = take_event(p);
+      if (a) cudaEventRecord(a, p->stream);
+    }
+  }
+  ~Stage() {
+    if (!a) return;
+    cudaEvent_t b = take_event(p);
+    if (!b) return;
+    cudaEventRecord(b, p->stream);
+    p->ev_marks.push_back({id, {a, b}});
+  }
+};
+
 cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   TRY(cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, p->stream));
   TRY(cudaStreamSynchronize(p->stream));
@@ -63,57 +109,64 @@ cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   return info->status == CQR2_OK ? CQR2_OK : CQR2_ERR_NOT_SPD;
 }
 
-// One CholeskyQR pass (Algorithm CQR) on X (m x n): W = X^T X; [L, Y] =
-// CholInv(W); Qout = X Y^T. For the small path Qout may alias X.
-// If `gram_done`, W already holds X^T X.
-cqr2_status_t cqr_pass(cqr2_plan_st* p, const double* X, int64_t ldx, double* Qout, int64_t ldq, int pass,
-                       bool gram_done) {
-  const int n = (int)p->n;
-  cudaStream_t s = p->stream;
-  if (!gram_done) {
-    TRY(gram_partials(X, ldx, p->m, n, p->g, p->partial, s));
-    TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
-  }
-  TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s));
-  if (p->small) {
-    TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
-    TRY(qform_small(X, ldx, p->m, n, p->Rp, Qout, ldq, s));
-  } else {
-    TRY(gemm_f64(p->m, n, n, 1.0, X, ldx, p->Y, n, 0.0, Qout, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
-  }
-  return CQR2_OK;
-}
-
 cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
                           int64_t ldr) {
   const int n = (int)p->n;
   cudaStream_t s = p->stream;
   TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   // ---- pass 1: W1 = A^T A, [L1, Y1] = CholInv(W1)
-  TRY(gram_partials(dA, lda, p->m, n, p->g, p->partial, s));
-  TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
-  TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
-  TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
-  cqr2_status_t r;
+  {
+    Stage st(p, CQR2_STAGE_GRAM1);
+    TRY(gram_partials(dA, lda, p->m, n, p->g, p->partial, s));
+    TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+  }
+  {
+    Stage st(p, CQR2_STAGE_CHOLINV1);
+    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
+    TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
+  }
+  // ---- Q1 = A R1^-1 (staged in dQ on the small path), then pass 2 on Q1
+  const double* X2 = dQ;
+  int64_t ldx2 = ldq;
   if (p->small) {
-    // Q1 = A R1^-1, staged in dQ
+    Stage st(p, CQR2_STAGE_QFORM1);
     TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
     if (p->fused) {
       // Q1 and the partial Grams of Q1 in one sweep over A
       TRY(qform_gram_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->g, p->partial, s));
-      TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
-      if ((r = cqr_pass(p, dQ, ldq, dQ, ldq, 2, true)) != CQR2_OK) return r;
     } else {
       TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, s));
-      if ((r = cqr_pass(p, dQ, ldq, dQ, ldq, 2, false)) != CQR2_OK) return r;
     }
   } else {
+    Stage st(p, CQR2_STAGE_QFORM1);
     TRY(gemm_f64(p->m, n, n, 1.0, dA, lda, p->Y, n, 0.0, p->Q1, p->m, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
-    if ((r = cqr_pass(p, p->Q1, p->m, dQ, ldq, 2, false)) != CQR2_OK) return r;
+    X2 = p->Q1;
+    ldx2 = p->m;
+  }
+  {
+    Stage st(p, CQR2_STAGE_GRAM2);
+    if (!p->fused) TRY(gram_partials(X2, ldx2, p->m, n, p->g, p->partial, s));
+    TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+  }
+  {
+    Stage st(p, CQR2_STAGE_CHOLINV2);
+    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 2, s));
+  }
+  {
+    Stage st(p, CQR2_STAGE_QFORM2);
+    if (p->small) {
+      TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
+      TRY(qform_small(dQ, ldq, p->m, n, p->Rp, dQ, ldq, s));  // in place, panel by panel
+    } else {
+      TRY(gemm_f64(p->m, n, n, 1.0, X2, ldx2, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    }
   }
   // ---- R = R2 R1 with R2 = L2^T
-  TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
-               GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+  {
+    Stage st(p, CQR2_STAGE_TRMM);
+    TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
+                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+  }
   return CQR2_OK;
 }
 
@@ -228,6 +281,10 @@ cqr2_status_t cqr2_plan_set_stream(cqr2_plan_t plan, void* stream) {
 void cqr2_plan_destroy(cqr2_plan_t plan) {
   if (!plan) return;
   cudaStreamSynchronize(plan->stream);
+  for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  cudaFree(plan->hA_dev);
+  cudaFree(plan->hQ_dev);
+  cudaFree(plan->hR_dev);
   cudaFree(plan->ws);
   cudaFreeHost(plan->h_st);
   delete plan;
@@ -261,8 +318,11 @@ cqr2_status_t cqr2_lstsq(cqr2_plan_t p, const double* dA, int64_t lda, const dou
   double* R = dR ? dR : p->Rf;
   const int64_t ldR = dR ? ldr : p->n;
   if ((r = factor_impl(p, dA, lda, dQ, ldq, R, ldR)) != CQR2_OK) return r;
-  TRY(gemv_t_partials(dQ, ldq, p->m, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
-  TRY(lstsq_solve(p->lspart, p->gemv_nsplit, (int)p->n, R, ldR, dx, p->stream));
+  {
+    Stage st(p, CQR2_STAGE_LSTSQ);
+    TRY(gemv_t_partials(dQ, ldq, p->m, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
+    TRY(lstsq_solve(p->lspart, p->gemv_nsplit, (int)p->n, R, ldR, dx, p->stream));
+  }
   if (info) return read_info(p, info);
   return CQR2_OK;
 }
@@ -315,6 +375,76 @@ cqr2_status_t cqr2_trmm_upper(cqr2_plan_t p, const double* dR2, int64_t ld2, con
   TRY(gemm_f64(n, n, n, 1.0, dR2, ld2, dR1, ld1, 0.0, dR, ldr,
                GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, p->stream));
   return CQR2_OK;
+}
+
+const char* cqr2_stage_name(int32_t stage) {
+  static const char* names[CQR2_NUM_STAGES] = {"gram1", "cholinv1", "qform1", "gram2", "cholinv2",
+                                               "qform2", "trmm",  "lstsq",  "h2d",   "d2h"};
+  return (stage >= 0 && stage < CQR2_NUM_STAGES) ? names[stage] : "unknown";
+}
+
+int64_t cqr2_launch_count(void) { return launch_count(); }
+
+cqr2_status_t cqr2_plan_set_profiling(cqr2_plan_t p, int32_t enable) {
+  if (!p) return CQR2_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+  p->profiling = enable != 0;
+  p->ev_marks.clear();
+  p->ev_used = 0;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_plan_stage_times(cqr2_plan_t p, double* ms, int64_t* count, int32_t nstages) {
+  if (!p || !ms || nstages < 0) return CQR2_ERR_INVALID_ARG;
+  for (int i = 0; i < nstages; ++i) {
+    ms[i] = 0.0;
+    if (count) count[i] = 0;
+  }
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+  for (auto& mk : p->ev_marks) {
+    if (mk.first >= nstages) continue;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, mk.second.first, mk.second.second) != cudaSuccess) return CQR2_ERR_CUDA;
+    ms[mk.first] += t;
+    if (count) count[mk.first] += 1;
+  }
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_factor_host(cqr2_plan_t p, const double* hA, int64_t lda, double* hQ, int64_t ldq, double* hR,
+                               int64_t ldr, cqr2_info_t* info) {
+  if (!p || !hA || !hQ || !hR) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, p->m) || bad_ld(ldq, p->m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
+  cqr2_status_t r = check_device(p);
+  if (r != CQR2_OK) return r;
+  const size_t mn = (size_t)p->m * p->n * sizeof(double);
+  if (!p->hA_dev) {
+    if (cudaMalloc(&p->hA_dev, mn) != cudaSuccess || cudaMalloc(&p->hQ_dev, mn) != cudaSuccess ||
+        cudaMalloc(&p->hR_dev, (size_t)p->n * p->n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p->hA_dev);
+      cudaFree(p->hQ_dev);
+      p->hA_dev = p->hQ_dev = nullptr;
+      return CQR2_ERR_OOM;
+    }
+  }
+  const size_t rowb = (size_t)p->m * sizeof(double);
+  {
+    Stage st(p, CQR2_STAGE_H2D);
+    TRY(cudaMemcpy2DAsync(p->hA_dev, rowb, hA, (size_t)lda * sizeof(double), rowb, (size_t)p->n,
+                          cudaMemcpyHostToDevice, p->stream));
+  }
+  if ((r = factor_impl(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n)) != CQR2_OK) return r;
+  {
+    Stage st(p, CQR2_STAGE_D2H);
+    TRY(cudaMemcpy2DAsync(hQ, (size_t)ldq * sizeof(double), p->hQ_dev, rowb, rowb, (size_t)p->n,
+                          cudaMemcpyDeviceToHost, p->stream));
+    TRY(cudaMemcpy2DAsync(hR, (size_t)ldr * sizeof(double), p->hR_dev, (size_t)p->n * sizeof(double),
+                          (size_t)p->n * sizeof(double), (size_t)p->n, cudaMemcpyDeviceToHost, p->stream));
+  }
+  cqr2_info_t local;
+  r = read_info(p, info ? info : &local);
+  return r;
 }
 
 }  // extern "C"

@@ -97,6 +97,7 @@ cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* 
                 int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s) {
   if (n <= NB) {
     k_cholinv_base<<<1, 256, BASE_SMEM, s>>>(Wk, ldk, n, L, ldl, Y, ldy, st, pass, off);
+    count_launch();
     return cudaGetLastError();
   }
   const int n1 = NB * (int)ceil_div(n, 2 * NB);
@@ -147,12 +148,14 @@ cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl,
 cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int64_t ldr, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32));
   k_transpose_lower<<<grid, dim3(32, 8), 0, s>>>(L, ldl, n, R, ldr);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t copy_upper(const double* X, int64_t ldx, int n, double* R, int64_t ldr, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(n, 128), (unsigned)n);
   k_copy_upper<<<grid, 128, 0, s>>>(X, ldx, n, R, ldr);
+  count_launch();
   return cudaGetLastError();
 }
 

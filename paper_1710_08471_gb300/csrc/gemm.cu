@@ -150,6 +150,7 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
   else if (!ta && tb) k_gemm_f64<false, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
   else if (ta && !tb) k_gemm_f64<true, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
   else k_gemm_f64<true, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -184,6 +184,7 @@ cudaError_t launch_tile(const double* A, int64_t lda, int64_t m, int n, const Gr
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)g.nsplit, (unsigned)ntiles_y);
   kern<<<grid, NT, sm, s>>>(A, lda, m, n, g.rows_per_split, g.ntile, g.ntiles_total, partial);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -230,6 +231,7 @@ cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double*
   dim3 block(128);
   dim3 grid((unsigned)ceil_div(n, 128), (unsigned)n);
   k_gram_reduce<<<grid, block, 0, s>>>(partial, g.nsplit, g.T, g.ntile, g.ntiles_total, n, W, ldw);
+  count_launch();
   return cudaGetLastError();
 }
 

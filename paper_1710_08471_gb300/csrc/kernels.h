@@ -9,6 +9,10 @@
 
 namespace cqr2 {
 
+// Process-wide count of kernel launches issued by this library.
+void count_launch();
+int64_t launch_count();
+
 // ---------------------------------------------------------------- Gram
 // Split-m Syrk W = A^T A (Section II-A; the tall dimension is cut into row
 // ranges whose partial Grams are summed in a fixed order, the single-GPU form

@@ -60,6 +60,7 @@ cudaError_t gemv_t_partials(const double* Q, int64_t ldq, int64_t m, int n, cons
                             double* partial, cudaStream_t s) {
   const int64_t rows_per = ceil_div(m, nsplit);
   k_gemv_t_partial<<<(unsigned)nsplit, GT, 0, s>>>(Q, ldq, m, n, b, rows_per, partial);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -71,6 +72,7 @@ cudaError_t lstsq_solve(const double* partial, int64_t nsplit, int n, const doub
     if (e != cudaSuccess) return e;
   }
   k_lstsq_solve<<<1, 1024, sm, s>>>(partial, nsplit, n, R, ldr, x);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -213,6 +213,7 @@ cudaError_t launch_qform(const double* A, int64_t lda, int64_t m, int n, const d
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QT, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(npanels, (int64_t)sm_count() * std::max(1, per_sm)));
   kern<<<(unsigned)grid, QT, sm, s>>>(A, lda, m, n, Rp, Q, ldq, npanels);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -224,6 +225,7 @@ cudaError_t launch_fused(const double* A, int64_t lda, int64_t m, int n, const d
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)g.nsplit, QT, sm, s>>>(A, lda, m, n, Rp, Q, ldq, g.rows_per_split, g.ntiles_total, partial);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -248,6 +250,7 @@ static cudaError_t pack(const double* X, int64_t ldx, int n, bool lower, double*
   const int64_t total = (int64_t)NGROUP * n * w;
   const int grid = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
   k_pack_rinv<<<grid, 256, 0, s>>>(X, ldx, n, w, lower, Rp);
+  count_launch();
   return cudaGetLastError();
 }
 
