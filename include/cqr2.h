@@ -140,6 +140,38 @@ cqr2_status_t cqr2_qform(cqr2_plan_t plan, const double* dA, int64_t lda, const 
 cqr2_status_t cqr2_trmm_upper(cqr2_plan_t plan, const double* dR2, int64_t ld2, const double* dR1,
                               int64_t ld1, double* dR, int64_t ldr);
 
+/* ---- Allocation-free Gram ---- */
+
+/* Fixed device scratch of cqr2_syrk_noalloc (32 MiB per GPU) and the largest
+ * n it serves. */
+#define CQR2_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define CQR2_NOALLOC_MAX_N 2816
+
+/* W = A^T A, the same Gram as cqr2_syrk, for callers that cannot allocate
+ * device memory. The paper has no counterpart: it exists because some
+ * callers must not call cudaMalloc, for example a host program that hands all
+ * device memory to its own pool allocator up front, or code running where a
+ * device allocation could fail under memory pressure or stall other work in
+ * the middle of a job. This entry point needs no plan and calls no
+ * cudaMalloc, cudaFree or allocating library routine: its split-m partial
+ * Gram tiles live in one file-scope device array of
+ * CQR2_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds
+ * until the process exits.
+ *   dA: m x n (lda >= m) device input; dW: n x n (ldw >= n) device output,
+ *   both triangles written. stream: cudaStream_t as void* (NULL = default).
+ *   Errors: CQR2_ERR_INVALID_ARG for null pointers, n < 1, m < n or a bad
+ *   leading dimension; CQR2_ERR_UNSUPPORTED for n > CQR2_NOALLOC_MAX_N (the
+ *   partial tiles of one row range would not fit the scratch); CQR2_ERR_CUDA
+ *   if a CUDA call fails. Larger m only means fewer row ranges.
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current) and caches it; make that first call before any
+ * stream capture. All calls share the one array and it keeps the last call's
+ * contents; every entry a call reads is written earlier in the same call, so
+ * nothing needs clearing, but calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on the array: serialize them. */
+cqr2_status_t cqr2_syrk_noalloc(const double* dA, int64_t m, int64_t n, int64_t lda, double* dW, int64_t ldw,
+                                void* stream);
+
 /* ---- Host-buffer entry point ---- */
 
 /* CholeskyQR2 of a matrix in HOST memory: copies hA (m x n, lda) to the

@@ -164,6 +164,14 @@ def cqr2_trmm_upper(plan, n, R2, R1, R) -> None:
     N.check(N.load().cqr2_trmm_upper(plan, r2, ld2, r1, ld1, r, ldr), "cqr2_trmm_upper")
 
 
+def cqr2_syrk_noalloc(m, n, A, W, stream=None) -> None:
+    """W = A^T A without any device allocation (fixed library scratch); for
+    callers that must not allocate device memory. n <= 2816."""
+    a, lda = _mat(A, m, n, "A")
+    w, ldw = _mat(W, n, n, "W")
+    N.check(N.load().cqr2_syrk_noalloc(a, m, n, lda, w, ldw, _stream_handle(stream)), "cqr2_syrk_noalloc")
+
+
 def cqr2_factor_host(plan, m, n, hA, hQ, hR) -> Info:
     """Host-buffer CholeskyQR2. hA, hQ, hR are Fortran-ordered float64 numpy
     arrays (pinned or pageable) of shapes (m, n), (m, n), (n, n)."""

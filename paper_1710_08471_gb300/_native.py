@@ -48,6 +48,7 @@ SIGNATURES = {
     "cqr2_cholinv": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_qform": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64]),
     "cqr2_trmm_upper": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64]),
+    "cqr2_syrk_noalloc": (C.c_int, [_D, _I64, _I64, _I64, _D, _I64, _P]),
     "cqr2_factor_host": (C.c_int, [_P, _P, _I64, _P, _I64, _P, _I64, C.POINTER(Info)]),
     "cqr2_plan_set_profiling": (C.c_int, [_P, C.c_int32]),
     "cqr2_plan_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),

@@ -15,13 +15,22 @@
 // cp.async; the layout [row][column] (padded) makes lanes that differ in the
 // column index hit distinct banks.
 #include <algorithm>
+#include <mutex>
 
+#include "../../include/cqr2.h"
 #include "kernels.h"
 
 namespace cqr2 {
 namespace {
 
 constexpr int KC = 32;  // rows per staged chunk
+
+// Scratch of the allocation-free Gram entry point (cqr2_syrk_noalloc): the
+// split-m partial tiles live in this fixed device array instead of a plan's
+// workspace. Every GPU that loads this library holds it until the process
+// exits.
+constexpr size_t NOALLOC_DOUBLES = CQR2_NOALLOC_SCRATCH_BYTES / sizeof(double);
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
 template <int T>
 __host__ __device__ constexpr int lds() {
@@ -236,3 +245,52 @@ cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double*
 }
 
 }  // namespace cqr2
+
+namespace {
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) on the first call there. Host code must not use the
+// symbol itself: on the host it names a stand-in, not device memory.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_addr[MAX_DEVICES] = {};
+
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, cqr2::g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" cqr2_status_t cqr2_syrk_noalloc(const double* dA, int64_t m, int64_t n, int64_t lda, double* dW,
+                                           int64_t ldw, void* stream) {
+  using namespace cqr2;
+  if (!dA || !dW || n < 1 || m < n || lda < m || ldw < n) return CQR2_ERR_INVALID_ARG;
+  if (n > CQR2_NOALLOC_MAX_N) return CQR2_ERR_UNSUPPORTED;
+  const GramGeom g0 = gram_geometry(m, (int)n, 0);
+  const int64_t per_split = (int64_t)g0.ntiles_total * g0.T * g0.T;
+  const int64_t max_splits = (int64_t)NOALLOC_DOUBLES / per_split;
+  if (max_splits < 1) return CQR2_ERR_UNSUPPORTED;
+  const GramGeom g = gram_geometry(m, (int)n, max_splits);
+  if (g.partial_doubles() > NOALLOC_DOUBLES) return CQR2_ERR_UNSUPPORTED;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return CQR2_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Every partial entry the reduction reads is written by gram_partials in
+  // this same call, so nothing left over from an earlier call is used and no
+  // clearing is needed.
+  if (gram_partials(dA, lda, m, (int)n, g, scratch, s) != cudaSuccess) return CQR2_ERR_CUDA;
+  if (gram_reduce(scratch, g, (int)n, dW, ldw, s) != cudaSuccess) return CQR2_ERR_CUDA;
+  return CQR2_OK;
+}
