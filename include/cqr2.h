@@ -56,10 +56,13 @@ typedef enum {
 
 /* Arithmetic of the two O(m n^2) contractions (Gram and Q-forming).
  * CQR2_FP64: native FP64 FMA throughout.
- * CQR2_OZAKI_BF16: the Gram and Q-forming products are emulated with
- *   BF16 tensor-core products of error-free slices (Ozaki scheme); CholInv and
- *   R = R2 R1 stay native FP64. Not part of the paper. */
-typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1 } cqr2_precision_t;
+ * CQR2_OZAKI_BF16: the Gram and Q-forming products are emulated on the
+ *   BF16 tensor cores from 7 error-free slices of every FP64 entry (about 55
+ *   significant bits, Ozaki scheme) with exact accumulation; CholInv and
+ *   R = R2 R1 stay native FP64. Not part of the paper. n <= 1024.
+ * CQR2_OZAKI_BF16_S6: the same with 6 slices (about 47 bits): faster, with
+ *   errors within 10x of the FP64 bounds for kappa(A) <= 1e6. */
+typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2_precision_t;
 
 /* Plan flags. */
 #define CQR2_FUSED 0x1u /* fuse pass-1 Q-forming with the pass-2 Gram: Q1 is
@@ -68,7 +71,8 @@ typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1 } cqr2_precision_t;
 
 /* Device-side outcome of a factorization. */
 typedef struct {
-  int32_t status;       /* CQR2_OK or CQR2_ERR_NOT_SPD */
+  int32_t status;       /* CQR2_OK, CQR2_ERR_NOT_SPD, or CQR2_ERR_TIMEOUT when a
+                           bounded device-side wait of a tensor-core kernel gave up */
   int32_t failed_pass;  /* 0 = none, 1 or 2 = CholeskyQR pass that broke down */
   int64_t failed_pivot; /* 0-based index of the first bad pivot, -1 = none */
   double pivot_value;   /* value of that pivot (may be NaN) */

@@ -24,6 +24,7 @@ from ._native import (  # noqa: F401
     CQR2_FUSED,
     CQR2_OK,
     CQR2_OZAKI_BF16,
+    CQR2_OZAKI_BF16_S6,
     CQR2Error,
     Info,
 )

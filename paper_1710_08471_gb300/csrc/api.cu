@@ -47,6 +47,16 @@ struct cqr2_plan_st {
   double* hA_dev = nullptr;
   double* hQ_dev = nullptr;
   double* hR_dev = nullptr;
+  // split-precision (Ozaki) path
+  int oz_S = 0;  // slices per entry, 0 = native FP64
+  unsigned short* oz_planes = nullptr;
+  unsigned short* oz_rinv = nullptr;
+  unsigned long long* oz_colmax = nullptr;
+  int* oz_cexp = nullptr;
+  int* oz_rexp = nullptr;
+  int* oz_fexp = nullptr;
+  double* oz_partial = nullptr;
+  OzMaps oz_maps;
   // per-stage CUDA-event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -102,15 +112,55 @@ struct Stage {
 cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   TRY(cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, p->stream));
   TRY(cudaStreamSynchronize(p->stream));
-  info->status = p->h_st->status ? CQR2_ERR_NOT_SPD : CQR2_OK;
-  info->failed_pass = p->h_st->status ? p->h_st->pass : 0;
-  info->failed_pivot = p->h_st->status ? p->h_st->pivot : -1;
-  info->pivot_value = p->h_st->status ? p->h_st->value : 0.0;
-  return info->status == CQR2_OK ? CQR2_OK : CQR2_ERR_NOT_SPD;
+  const int st = p->h_st->status;
+  info->status = st == 0 ? CQR2_OK : (st == 5 ? CQR2_ERR_TIMEOUT : CQR2_ERR_NOT_SPD);
+  info->failed_pass = st == 2 ? p->h_st->pass : 0;
+  info->failed_pivot = st == 2 ? p->h_st->pivot : -1;
+  info->pivot_value = st == 2 ? p->h_st->value : 0.0;
+  return (cqr2_status_t)info->status;
+}
+
+// Split-precision CholeskyQR2: the Gram and Q-forming contractions on the
+// BF16 tensor cores (Ozaki slices), CholInv and R2 R1 in native FP64.
+cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                                int64_t ldr) {
+  const int n = (int)p->n, S = p->oz_S;
+  const int64_t m = p->m;
+  cudaStream_t s = p->stream;
+  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  for (int pass = 1; pass <= 2; ++pass) {
+    const double* X = pass == 1 ? dA : dQ;
+    const int64_t ldx = pass == 1 ? lda : ldq;
+    {
+      Stage st(p, pass == 1 ? CQR2_STAGE_GRAM1 : CQR2_STAGE_GRAM2);
+      TRY(ozaki_colmax(X, ldx, m, n, p->oz_colmax, p->oz_cexp, s));
+      TRY(ozaki_slice_cols(X, ldx, m, n, S, p->oz_cexp, p->oz_planes, s));
+      TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->W, n, p->st, s));
+    }
+    {
+      Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
+      TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s));
+      if (pass == 1) TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
+    }
+    {
+      // Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
+      Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
+      TRY(ozaki_slice_rinv(p->Y, n, n, S, false, p->oz_rinv, p->oz_fexp, s));
+      TRY(ozaki_slice_rows(X, ldx, m, n, S, p->oz_planes, p->oz_rexp, s));
+      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, s));
+    }
+  }
+  {
+    Stage st(p, CQR2_STAGE_TRMM);
+    TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
+                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+  }
+  return CQR2_OK;
 }
 
 cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
                           int64_t ldr) {
+  if (p->oz_S) return factor_impl_ozaki(p, dA, lda, dQ, ldq, dR, ldr);
   const int n = (int)p->n;
   cudaStream_t s = p->stream;
   TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
@@ -198,8 +248,11 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (!plan) return CQR2_ERR_INVALID_ARG;
   *plan = nullptr;
   if (n < 1 || m < n || n > 65535) return CQR2_ERR_INVALID_ARG;
-  if (precision != CQR2_FP64) return CQR2_ERR_UNSUPPORTED;
+  if (precision != CQR2_FP64 && precision != CQR2_OZAKI_BF16 && precision != CQR2_OZAKI_BF16_S6)
+    return CQR2_ERR_INVALID_ARG;
   if (flags & ~CQR2_FUSED) return CQR2_ERR_INVALID_ARG;
+  const int oz_S = precision == CQR2_OZAKI_BF16 ? 7 : (precision == CQR2_OZAKI_BF16_S6 ? 6 : 0);
+  if (oz_S && !ozaki_supported((int)n, oz_S)) return CQR2_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CQR2_ERR_CUDA;
   auto* p = new (std::nothrow) cqr2_plan_st();
@@ -214,8 +267,15 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->small = qform_group_width((int)n) > 0;
   p->fused = (flags & CQR2_FUSED) && qform_gram_fusable((int)n);
   p->gemv_nsplit = gemv_splits(m, (int)n);
+  p->oz_S = oz_S;
   const size_t nn = (size_t)n * n * sizeof(double);
-  size_t off[16];
+  OzGeom og;
+  if (oz_S) {
+    og = ozaki_geometry(m, (int)n);
+    p->small = false;  // no m x n FP64 workspace: Q1 is staged in the output Q
+    p->fused = false;
+  }
+  size_t off[24];
   size_t sz = 0;
   int k = 0;
   auto take = [&](size_t bytes) {
@@ -231,9 +291,18 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   take(nn);                                                          // 6 R1
   take(nn);                                                          // 7 Rf
   take(rpack_doubles((int)n) * sizeof(double));                      // 8 Rp
-  take(p->small ? 0 : (size_t)m * n * sizeof(double));               // 9 Q1
+  take((p->small || oz_S) ? 0 : (size_t)m * n * sizeof(double));    // 9 Q1
   take((size_t)p->gemv_nsplit * n * sizeof(double));                 // 10 lspart
   take(sizeof(DevStatus));                                           // 11 st
+  if (oz_S) {
+    take(ozaki_plane_elems(m, (int)n, oz_S) * 2);                    // 12 slice planes (bf16)
+    take((size_t)oz_S * n * og.np * 2);                              // 13 R^-1 planes
+    take((size_t)n * sizeof(unsigned long long));                    // 14 column max
+    take((size_t)n * sizeof(int));                                   // 15 column exponents
+    take((size_t)m * sizeof(int));                                   // 16 row exponents
+    take((size_t)n * sizeof(int));                                   // 17 R^-1 exponents
+    take((size_t)og.nsplit * n * n * sizeof(double));                // 18 Gram partials
+  }
   if (cudaMalloc(&p->ws, sz) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -259,6 +328,25 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->Q1 = p->small ? nullptr : at(9);
   p->lspart = at(10);
   p->st = reinterpret_cast<DevStatus*>(p->ws + off[11]);
+  if (oz_S) {
+    p->oz_planes = reinterpret_cast<unsigned short*>(p->ws + off[12]);
+    p->oz_rinv = reinterpret_cast<unsigned short*>(p->ws + off[13]);
+    p->oz_colmax = reinterpret_cast<unsigned long long*>(p->ws + off[14]);
+    p->oz_cexp = reinterpret_cast<int*>(p->ws + off[15]);
+    p->oz_rexp = reinterpret_cast<int*>(p->ws + off[16]);
+    p->oz_fexp = reinterpret_cast<int*>(p->ws + off[17]);
+    p->oz_partial = at(18);
+    // zero the planes once so that padding rows/columns read as zero
+    if (cudaMemsetAsync(p->oz_planes, 0, ozaki_plane_elems(m, (int)n, oz_S) * 2, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->oz_rinv, 0, (size_t)oz_S * n * og.np * 2, p->stream) != cudaSuccess ||
+        ozaki_make_maps(p->oz_maps, m, (int)n, oz_S, p->oz_planes, p->oz_rinv) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(p->h_st);
+      cudaFree(p->ws);
+      delete p;
+      return CQR2_ERR_CUDA;
+    }
+  }
   std::memset(p->h_st, 0, sizeof(DevStatus));
   if (cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream) != cudaSuccess) {
     cudaFreeHost(p->h_st);
@@ -331,6 +419,14 @@ cqr2_status_t cqr2_syrk(cqr2_plan_t p, const double* dA, int64_t lda, double* dW
   if (!p || !dA || !dW || bad_ld(lda, p->m) || bad_ld(ldw, p->n)) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if (p->oz_S) {
+    const int n = (int)p->n;
+    TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
+    TRY(ozaki_colmax(dA, lda, p->m, n, p->oz_colmax, p->oz_cexp, p->stream));
+    TRY(ozaki_slice_cols(dA, lda, p->m, n, p->oz_S, p->oz_cexp, p->oz_planes, p->stream));
+    TRY(ozaki_gram(p->oz_maps, p->m, n, p->oz_S, p->oz_cexp, p->oz_partial, dW, ldw, p->st, p->stream));
+    return CQR2_OK;
+  }
   TRY(gram_partials(dA, lda, p->m, (int)p->n, p->g, p->partial, p->stream));
   TRY(gram_reduce(p->partial, p->g, (int)p->n, dW, ldw, p->stream));
   return CQR2_OK;
@@ -356,7 +452,12 @@ cqr2_status_t cqr2_qform(cqr2_plan_t p, const double* dA, int64_t lda, const dou
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
   const int n = (int)p->n;
-  if (p->small) {
+  if (p->oz_S) {
+    TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
+    TRY(ozaki_slice_rinv(dRinv, ldri, n, p->oz_S, true, p->oz_rinv, p->oz_fexp, p->stream));
+    TRY(ozaki_slice_rows(dA, lda, p->m, n, p->oz_S, p->oz_planes, p->oz_rexp, p->stream));
+    TRY(ozaki_qform(p->oz_maps, p->m, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, p->stream));
+  } else if (p->small) {
     TRY(pack_rinv_from_upper(dRinv, ldri, n, p->Rp, p->stream));
     TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->stream));
   } else {

@@ -78,6 +78,41 @@ cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int6
 // R = upper part of X with zeros below the diagonal.
 cudaError_t copy_upper(const double* X, int64_t ldx, int n, double* R, int64_t ldr, cudaStream_t s);
 
+// ---------------------------------------------------------------- Ozaki
+// Split-precision Gram and Q-form on BF16 tensor cores (see ozaki.cu).
+constexpr int OZAKI_MAX_N = 1024;
+struct OzGeom {
+  int64_t mp = 0;            // m rounded up to 64
+  int np = 0;                // n rounded up to 64
+  int ntile_j = 0;           // 64-column tiles
+  int ntiles = 0;            // Gram tiles (128 x 64) touching the upper triangle
+  int64_t rows_per_split = 0;
+  int nsplit = 0;
+};
+// Four TMA descriptors (CUtensorMap is 128 bytes, 64-byte aligned).
+struct OzMaps {
+  alignas(64) unsigned char col_a[128];
+  alignas(64) unsigned char col_b[128];
+  alignas(64) unsigned char row_a[128];
+  alignas(64) unsigned char rinv_b[128];
+};
+bool ozaki_supported(int n, int S);
+OzGeom ozaki_geometry(int64_t m, int n);
+size_t ozaki_plane_elems(int64_t m, int n, int S);
+cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes, void* rinv_planes);
+cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned long long* colmax, int* cexp,
+                         cudaStream_t s);
+cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int S, const int* cexp,
+                             unsigned short* planes, cudaStream_t s);
+cudaError_t ozaki_slice_rows(const double* X, int64_t ld, int64_t m, int n, int S, unsigned short* planes, int* rexp,
+                             cudaStream_t s);
+cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, unsigned short* planes,
+                             int* fexp, cudaStream_t s);
+cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial, double* W,
+                       int64_t ldw, DevStatus* st, cudaStream_t s);
+cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* rexp, const int* fexp, double* Q,
+                        int64_t ldq, DevStatus* st, cudaStream_t s);
+
 // ---------------------------------------------------------------- lstsq
 // c = Q^T b as split-m partials, then x solves R x = c (back substitution).
 int64_t gemv_splits(int64_t m, int n);
