@@ -227,6 +227,38 @@ def bench_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+PRECISIONS = {"fp64": 0, "ozaki": 1, "ozaki6": 2}
+SLICES = {"fp64": 0, "ozaki": 7, "ozaki6": 6}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "src": "fallback"}
+
+
+def stage_work(m: int, n: int, precision: str, fused: bool) -> dict:
+    """Algorithmic work per stage instance: FP64 flops (native) or BF16
+    tensor-core flops of the kept slice products (split precision)."""
+    S = SLICES[precision]
+    tri = m * n * (n + 1)  # one Syrk or one triangular Q-form, 2 flops per FMA
+    if S == 0:
+        return {"gram1": tri, "qform1": 2 * tri if fused else tri, "gram2": 0 if fused else tri, "qform2": tri,
+                "cholinv1": 2 * n ** 3 / 3, "cholinv2": 2 * n ** 3 / 3, "trmm": n ** 3 / 3}
+    P = S * (S + 1) // 2
+    ntj = -(-n // 64)
+    np_ = ntj * 64
+    ntiles = sum(ntj - 2 * i for i in range(ntj) if 2 * i < ntj)
+    gram = ntiles * 2 * 128 * 64 * m * P
+    qform = 2 * 128 * 64 * P * (-(-m // 128)) * sum(min(64 * (j + 1), np_) for j in range(ntj))
+    return {"gram1": gram, "gram2": gram, "qform1": qform, "qform2": qform}
+
+
 def bench_ours(args, ws, rank, local):
     import torch
 
@@ -235,7 +267,8 @@ def bench_ours(args, ws, rank, local):
     m, n, kappa, seed, desc = WORKLOADS[args.workload]
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    fused = args.variant == "fused"
+    fused = args.variant == "fused" and args.precision == "fp64"
+    peaks = measured_peaks()
     # inputs: generated on the host (seed + rank), kept pinned for the e2e leg
     hA, hA_t = make_input(m, n, kappa, seed + 1000 * rank, pinned=True)
     A = cq.empty_colmajor(m, n, device=dev)
@@ -244,12 +277,14 @@ def bench_ours(args, ws, rank, local):
     R = cq.empty_colmajor(n, n, device=dev)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    plan = cq.Plan(m, n, fused=fused, stream=stream)
-    info = plan.factor(A, Q, R, sync=True)[2]
-    if info.status != 0:
-        raise SystemExit(f"factorization failed: {info.status}")
+
+    def make_plan(precision, fz):
+        return cq.Plan(m, n, precision=PRECISIONS[precision], fused=fz, stream=stream)
 
     def timed(pl, steps, warmup, profile):
+        info = pl.factor(A, Q, R, sync=True)[2]
+        if info.status != 0:
+            raise SystemExit(f"factorization failed: status {info.status}")
         for _ in range(warmup):
             pl.factor(A, Q, R, sync=False)
         torch.cuda.synchronize()
@@ -267,61 +302,100 @@ def bench_ours(args, ws, rank, local):
         ms = e0.elapsed_time(e1) / steps
         st = pl.stage_times() if profile else None
         pl.set_profiling(False)
-        return ms, launches, st
+        return ms, launches, {k: v[0] / v[1] for k, v in st.items() if v[1] > 0} if st else {}
 
+    def roofline_of(per_stage, precision, fz, clk):
+        work = stage_work(m, n, precision, fz)
+        cands = {k: v for k, v in per_stage.items() if k in work and work[k] > 0}
+        dom = max(cands, key=cands.get)
+        achieved = work[dom] / (per_stage[dom] * 1e-3) / 1e12
+        if SLICES[precision] == 0:
+            sm_max = clk.get("sm_max_mhz") or 2070.0
+            peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
+            kern = {"qform1": "k_qform_gram_small" if fz else "k_qform_small", "gram1": "k_gram_tile",
+                    "gram2": "k_gram_tile", "qform2": "k_qform_small"}.get(dom, dom)
+            kfile = "qform.cu" if "qform" in kern else "gram.cu"
+            note = f"derived FP64 DFMA peak: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 flops x {sm_max:.0f} MHz"
+            bound = "alu"
+        else:
+            peak = peaks["bf16_sustained"]
+            kern = "k_ozaki_gemm<%d,%s>" % (SLICES[precision], "GRAM" if dom.startswith("gram") else "QFORM")
+            kfile = "ozaki.cu"
+            note = f"{peaks['src']} sustained bf16 tensor peak; work = BF16 flops of the kept slice products"
+            bound = "tensor"
+        traffic = NCU_TRAFFIC.get(f"{kern}@{args.workload}@{src_sha(kfile)}")
+        return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
+
+    plan = make_plan(args.precision, fused)
     clocks = ClockSampler(local)
     clocks.start()
-    ms_local, launches, stages = timed(plan, args.steps, args.warmup, True)
+    ms_local, launches, per_stage = timed(plan, args.steps, args.warmup, True)
     clk = clocks.stop()
     ms_step = allreduce_max(ms_local, ws)
     flops = nominal_flops(m, n)
     value = ws * flops / (ms_step * 1e-3) / 1e12
-
-    # dominant stage -> roofline (FP64 ALU bound)
-    per_stage = {k: v[0] / v[1] for k, v in stages.items() if v[1] > 0}
-    dom = max(per_stage, key=per_stage.get)
-    tri = m * n * (n + 1)  # flops of one Syrk or one triangular Q-form (FMA = 2 flops)
-    stage_flops = {"gram1": tri, "qform1": 2 * tri if fused else tri, "gram2": 0 if fused else tri,
-                   "qform2": tri, "cholinv1": 2 * n ** 3 / 3, "cholinv2": 2 * n ** 3 / 3, "trmm": n ** 3 / 3}
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
-    achieved = stage_flops.get(dom, 0) / (per_stage[dom] * 1e-3) / 1e12
-    kern = {"qform1": "k_qform_gram_small" if fused else "k_qform_small", "gram1": "k_gram_tile",
-            "gram2": "k_gram_tile", "qform2": "k_qform_small"}.get(dom, dom)
-    kfile = "qform.cu" if "qform" in kern else "gram.cu"
-    traffic = NCU_TRAFFIC.get(f"{kern}@{args.workload}@{src_sha(kfile)}")
-    roofline = {"bound": "alu", "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_note": f"FP64 DFMA: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 flops x {sm_max:.0f} MHz"}
-    whole = {"achieved": value / ws, "frac": value / ws / peak}
+    fp64_peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
 
     out = {
         "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "m": m, "n": n, "kappa": kappa, "variant": args.variant,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-slices->f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
+                   "variant": "fused" if fused else "plain",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"},
         "gpu_launches": launches,
-        "roofline": roofline,
-        "whole_step_vs_fp64_peak": whole,
+        "roofline": roofline_of(per_stage, args.precision, fused, clk),
+        "vs_fp64_peak": {"achieved": value / ws, "peak": fp64_peak, "frac": value / ws / fp64_peak},
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "clocks": clk,
     }
     if rank == 0 and not args.quick:
-        # the other variant at the same size, for context
-        other = cq.Plan(m, n, fused=not fused, stream=stream)
-        ms_o, _, st_o = timed(other, max(2, args.steps // 2), 1, True)
-        out["variants"] = {("plain" if fused else "fused"): {
-            "ms_per_step": ms_o, "tflops": flops / (ms_o * 1e-3) / 1e12,
-            "stages_ms": {k: round(v[0] / v[1], 4) for k, v in st_o.items() if v[1] > 0}}}
-        other.close()
-        # end to end through the host-buffer C entry point
+        import oracle
+
         hQ, hQ_t = pinned_colmajor(m, n)
         hR, hR_t = pinned_colmajor(n, n)
+        # CPU FP64 oracle of the same workload: errors and the CPU baseline
+        rows, dt, Qo, Ro = run_oracle_sample(hA, args.oracle_rows or m)
+        sample = (f"full workload ({desc})" if rows == m else f"first {rows} of {m} rows of the workload ({desc})")
+        out["cpu_baseline"] = {"value": nominal_flops(rows, n) / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+                               "kind": "oracle", "sample": sample + "; numpy FP64 oracle, one run",
+                               "seconds": dt}
+        ref = {"oracle_orthogonality": oracle.orthogonality(Qo), "oracle_residual": oracle.residual(hA, Qo, Ro)}
+        del Qo
+
+        def errors():
+            hQ_t.copy_(Q.t())
+            hR_t.copy_(R.t())
+            torch.cuda.synchronize()
+            e = {"orthogonality": oracle.orthogonality(hQ), "residual": oracle.residual(hA, hQ, hR)}
+            if rows == m:
+                e["R_rel_vs_oracle"] = oracle.rel_error(np.asfortranarray(hR), Ro)
+            return e
+
+        plan.factor(A, Q, R, sync=True)
+        out["errors"] = dict(errors(), **ref)
+        # other variants of the same factorization at the same size
+        variants = {}
+        todo = [("fp64", not fused), ("ozaki", False), ("ozaki6", False)] if args.precision == "fp64" else \
+            [("fp64", True)] + [(p, False) for p in ("ozaki", "ozaki6") if p != args.precision]
+        for prec, fz in todo:
+            if SLICES[prec] and n > 1024:
+                continue
+            pl = make_plan(prec, fz)
+            ms_v, _, st_v = timed(pl, max(2, args.steps // 2), 1, True)
+            name = prec + ("_fused" if fz and prec == "fp64" else "")
+            variants[name] = {"ms_per_step": ms_v, "tflops": flops / (ms_v * 1e-3) / 1e12,
+                              "speedup_vs_main": ms_step / ms_v,
+                              "stages_ms": {k: round(v, 4) for k, v in st_v.items()},
+                              "roofline": roofline_of(st_v, prec, fz, clk), "errors": errors()}
+            pl.close()
+        out["variants"] = variants
+        # end to end through the host-buffer C entry point
         plan.factor_host(hA, hQ, hR)  # allocates staging
         times = []
-        l0 = cq.cqr2_launch_count()
         for _ in range(max(2, args.steps // 2)):
             t0 = time.perf_counter()
             plan.factor_host(hA, hQ, hR)
@@ -330,22 +404,6 @@ def bench_ours(args, ws, rank, local):
         out["e2e"] = {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                       "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8,
                       "api": "cqr2_factor_host (pinned host buffers)"}
-        # errors against the CPU FP64 oracle and the oracle's own time
-        Qh = hQ
-        Rh = np.asfortranarray(hR)
-        rows, dt, Qo, Ro = run_oracle_sample(hA, args.oracle_rows or m)
-        import oracle
-
-        err = {"orthogonality": oracle.orthogonality(Qh), "residual": oracle.residual(hA, Qh, Rh)}
-        if rows == m:
-            err["R_rel_vs_oracle"] = oracle.rel_error(Rh, Ro)
-            err["oracle_orthogonality"] = oracle.orthogonality(Qo)
-            err["oracle_residual"] = oracle.residual(hA, Qo, Ro)
-        out["errors"] = err
-        sample = (f"full workload ({desc})" if rows == m else f"first {rows} of {m} rows of the workload ({desc})")
-        out["cpu_baseline"] = {"value": nominal_flops(rows, n) / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
-                               "kind": "oracle", "sample": sample + "; numpy FP64 oracle, one run",
-                               "seconds": dt}
     plan.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -359,6 +417,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tall")
     ap.add_argument("--variant", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64",
+                    help="fp64: native FP64; ozaki / ozaki6: BF16 tensor-core slices (7 / 6 per entry)")
     ap.add_argument("--oracle-rows", type=int, default=None,
                     help="rows of the workload the CPU oracle runs on (default: all for the error check, "
                          "2^21 for --impl reference)")

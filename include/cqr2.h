@@ -191,7 +191,9 @@ cqr2_status_t cqr2_factor_host(cqr2_plan_t plan, const double* hA, int64_t lda, 
 
 /* Stages of a factorization timed by the per-plan profiler. With
  * CQR2_FUSED, CQR2_STAGE_QFORM1 also accumulates pass 2's partial Grams and
- * CQR2_STAGE_GRAM2 only sums them. */
+ * CQR2_STAGE_GRAM2 only sums them. With a split-precision plan, the slicing
+ * of the operands into BF16 digits is timed as CQR2_STAGE_SPLIT and the
+ * GRAM/QFORM stages hold the tensor-core contractions alone. */
 typedef enum {
   CQR2_STAGE_GRAM1 = 0,
   CQR2_STAGE_CHOLINV1 = 1,
@@ -203,7 +205,8 @@ typedef enum {
   CQR2_STAGE_LSTSQ = 7,
   CQR2_STAGE_H2D = 8,
   CQR2_STAGE_D2H = 9,
-  CQR2_NUM_STAGES = 10
+  CQR2_STAGE_SPLIT = 10,
+  CQR2_NUM_STAGES = 11
 } cqr2_stage_t;
 
 /* Turn per-stage timing on (1) or off (0) and clear what was recorded. While

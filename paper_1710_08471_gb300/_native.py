@@ -23,7 +23,7 @@ CQR2_FP64 = 0
 CQR2_OZAKI_BF16 = 1
 CQR2_OZAKI_BF16_S6 = 2
 CQR2_FUSED = 0x1
-CQR2_NUM_STAGES = 10
+CQR2_NUM_STAGES = 11
 
 
 class Info(C.Structure):

@@ -132,9 +132,12 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     const double* X = pass == 1 ? dA : dQ;
     const int64_t ldx = pass == 1 ? lda : ldq;
     {
-      Stage st(p, pass == 1 ? CQR2_STAGE_GRAM1 : CQR2_STAGE_GRAM2);
+      Stage st(p, CQR2_STAGE_SPLIT);
       TRY(ozaki_colmax(X, ldx, m, n, p->oz_colmax, p->oz_cexp, s));
       TRY(ozaki_slice_cols(X, ldx, m, n, S, p->oz_cexp, p->oz_planes, s));
+    }
+    {
+      Stage st(p, pass == 1 ? CQR2_STAGE_GRAM1 : CQR2_STAGE_GRAM2);
       TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->W, n, p->st, s));
     }
     {
@@ -143,10 +146,13 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
       if (pass == 1) TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
     }
     {
-      // Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
-      Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
+      Stage st(p, CQR2_STAGE_SPLIT);
       TRY(ozaki_slice_rinv(p->Y, n, n, S, false, p->oz_rinv, p->oz_fexp, s));
       TRY(ozaki_slice_rows(X, ldx, m, n, S, p->oz_planes, p->oz_rexp, s));
+    }
+    {
+      // The Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
+      Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
       TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, s));
     }
   }
@@ -480,7 +486,7 @@ cqr2_status_t cqr2_trmm_upper(cqr2_plan_t p, const double* dR2, int64_t ld2, con
 
 const char* cqr2_stage_name(int32_t stage) {
   static const char* names[CQR2_NUM_STAGES] = {"gram1", "cholinv1", "qform1", "gram2", "cholinv2",
-                                               "qform2", "trmm",  "lstsq",  "h2d",   "d2h"};
+                                               "qform2", "trmm",  "lstsq",  "h2d",   "d2h", "split"};
   return (stage >= 0 && stage < CQR2_NUM_STAGES) ? names[stage] : "unknown";
 }
 
