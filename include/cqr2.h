@@ -67,7 +67,12 @@ typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2
 /* Plan flags. */
 #define CQR2_FUSED 0x1u /* fuse pass-1 Q-forming with the pass-2 Gram: Q1 is
                            produced and its Gram accumulated in one sweep, so
-                           Q1 makes one fewer trip through memory */
+                           Q1 makes one fewer trip through memory (FP64,
+                           n <= 128; ignored otherwise) */
+#define CQR2_GRAPH 0x2u /* capture the launch sequence of a factorization in
+                           a CUDA graph and replay it while the call's
+                           pointers, leading dimensions and m repeat; needs a
+                           non-NULL stream; per-stage profiling bypasses it */
 
 /* Device-side outcome of a factorization. */
 typedef struct {
@@ -115,6 +120,22 @@ cqr2_status_t cqr2_factor(cqr2_plan_t plan, const double* dA, int64_t lda, doubl
 cqr2_status_t cqr2_lstsq(cqr2_plan_t plan, const double* dA, int64_t lda, const double* db, double* dx,
                          double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info);
 
+/* cqr2_factor / cqr2_lstsq for an m x n matrix with n <= m <= the plan's m
+ * (the plan's m is the largest row count it serves; its workspace is sized
+ * for it). Lets one plan per n serve matrices of uneven height. The launch
+ * geometry (row ranges, and tensor-map descriptors of a split-precision
+ * plan) is recomputed on the host when m changes between calls. */
+cqr2_status_t cqr2_factor_rows(cqr2_plan_t plan, int64_t m, const double* dA, int64_t lda, double* dQ,
+                               int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info);
+cqr2_status_t cqr2_lstsq_rows(cqr2_plan_t plan, int64_t m, const double* dA, int64_t lda, const double* db,
+                              double* dx, double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info);
+
+/* Tuning knobs of a plan (set by the autotuner, cqr2_autotune, or by hand):
+ * the number of Gram CTAs per SM (1..8, default 4), and whether to fuse the
+ * pass-1 Q-form with the pass-2 Gram (honoured only where CQR2_FUSED is). */
+cqr2_status_t cqr2_plan_set_gram_ctas(cqr2_plan_t plan, int32_t ctas_per_sm);
+cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t plan, int32_t fused);
+
 /* Synchronize the plan's stream and report the outcome of the last
  * factorization enqueued on the plan. */
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info);
@@ -143,6 +164,75 @@ cqr2_status_t cqr2_qform(cqr2_plan_t plan, const double* dA, int64_t lda, const 
  * strictly lower part of R set to 0. dR may not alias the inputs. */
 cqr2_status_t cqr2_trmm_upper(cqr2_plan_t plan, const double* dR2, int64_t ld2, const double* dR1,
                               int64_t ld1, double* dR, int64_t ldr);
+
+/* ---- Many independent factorizations ---- */
+
+/* One problem of a batch: A (m x n, lda) is factored into Q (m x n, ldq) and
+ * R (n x n, ldr), all device pointers, m >= n >= 1, Q not aliasing A. */
+typedef struct {
+  int64_t m, n;
+  const double* A;
+  int64_t lda;
+  double* Q;
+  int64_t ldq;
+  double* R;
+  int64_t ldr;
+} cqr2_problem_t;
+
+typedef struct cqr2_batch_st* cqr2_batch_t;
+
+/* Routing and concurrency of a batch.
+ * small_work_limit: problems with n <= 64 and m n^2 <= this are factored by
+ *   the persistent grouped kernel (one launch for all of them, one CTA per
+ *   problem at a time, FP64 whatever the batch precision).
+ * streams: the other problems run on per-(n, stream) plans spread over this
+ *   many streams (1..16) forked from and joined to the batch stream.
+ * fused: use CQR2_FUSED for those plans. */
+typedef struct {
+  int64_t small_work_limit;
+  int32_t streams;
+  int32_t fused;
+} cqr2_batch_config_t;
+
+/* Create a batch context for up to max_count problems per call, with the
+ * precision used by the planned problems (cqr2_precision_t). cfg may be NULL
+ * for the defaults (the tuned small-problem limit, 4 streams, fused). Plans
+ * are created lazily per (n, stream) and grow to the largest m seen. */
+cqr2_status_t cqr2_batch_create(cqr2_batch_t* batch, int32_t max_count, int32_t precision,
+                                const cqr2_batch_config_t* cfg, void* stream);
+
+/* Factor `count` problems (host array of descriptors). All work is enqueued
+ * on the batch's stream (and streams joined back into it). With infos (a host
+ * array of count entries) the call synchronizes and reports every problem's
+ * outcome, returning CQR2_ERR_NOT_SPD if any broke down; with NULL it is
+ * asynchronous. */
+cqr2_status_t cqr2_batch_factor(cqr2_batch_t batch, const cqr2_problem_t* problems, int32_t count,
+                                cqr2_info_t* infos);
+
+void cqr2_batch_destroy(cqr2_batch_t batch);
+
+/* ---- Autotuner ---- */
+
+typedef struct {
+  int32_t gram_ctas;   /* best Gram CTAs per SM */
+  int32_t fused;       /* best fusion choice */
+  double ms;           /* its time per factorization */
+  int32_t candidates;  /* configurations timed */
+} cqr2_tune_result_t;
+
+/* Time the candidate configurations (Gram CTAs per SM 1, 2, 4, 8; fused or
+ * not where fusion applies) of an m x n factorization at `precision` on the
+ * current device, with temporary device buffers, and record the fastest in a
+ * process-wide table keyed by (n, floor(log2 m), precision). Batches use the
+ * table for the plans they create. Synchronizes; allocates. */
+cqr2_status_t cqr2_autotune(int64_t m, int64_t n, int32_t precision, cqr2_tune_result_t* out);
+
+/* Set the batch routing limit on m n^2 used by batches created later. */
+cqr2_status_t cqr2_tune_set_small_limit(int64_t limit);
+
+/* Write the tuning table as text into buf (NUL-terminated, truncated to
+ * size); returns the size needed including the NUL. */
+int64_t cqr2_tune_table(char* buf, int64_t size);
 
 /* ---- Allocation-free Gram ---- */
 

@@ -135,6 +135,32 @@ def cqr2_lstsq(plan, m, n, A, b, x, Q, R=None, sync: bool = True) -> Info | None
     return info
 
 
+def cqr2_factor_rows(plan, m, n, A, Q, R, sync: bool = True) -> Info | None:
+    """cqr2_factor for an m-row matrix on a plan created for at least m rows."""
+    a, lda = _mat(A, m, n, "A")
+    q, ldq = _mat(Q, m, n, "Q")
+    r, ldr = _mat(R, n, n, "R")
+    info = Info() if sync else None
+    st = N.load().cqr2_factor_rows(plan, m, a, lda, q, ldq, r, ldr, C.byref(info) if sync else None)
+    N.check(st, "cqr2_factor_rows", info)
+    return info
+
+
+def cqr2_lstsq_rows(plan, m, n, A, b, x, Q, R=None, sync: bool = True) -> Info | None:
+    """cqr2_lstsq for an m-row matrix on a plan created for at least m rows."""
+    a, lda = _mat(A, m, n, "A")
+    q, ldq = _mat(Q, m, n, "Q")
+    if R is not None:
+        r, ldr = _mat(R, n, n, "R")
+    else:
+        r, ldr = None, n
+    info = Info() if sync else None
+    st = N.load().cqr2_lstsq_rows(plan, m, a, lda, _vec(b, m, "b"), _vec(x, n, "x"), q, ldq, r, ldr,
+                                  C.byref(info) if sync else None)
+    N.check(st, "cqr2_lstsq_rows", info)
+    return info
+
+
 def cqr2_syrk(plan, m, n, A, W) -> None:
     a, lda = _mat(A, m, n, "A")
     w, ldw = _mat(W, n, n, "W")
@@ -206,14 +232,121 @@ def cqr2_launch_count() -> int:
     return int(N.load().cqr2_launch_count())
 
 
+def cqr2_plan_set_gram_ctas(plan, ctas_per_sm: int) -> None:
+    N.check(N.load().cqr2_plan_set_gram_ctas(plan, ctas_per_sm), "cqr2_plan_set_gram_ctas")
+
+
+def cqr2_plan_set_fused(plan, fused: bool) -> None:
+    N.check(N.load().cqr2_plan_set_fused(plan, 1 if fused else 0), "cqr2_plan_set_fused")
+
+
+def cqr2_autotune(m: int, n: int, precision: int = CQR2_FP64) -> dict:
+    """Time candidate plan configurations for an m x n factorization and
+    record the best in the library's tuning table."""
+    res = N.TuneResult()
+    N.check(N.load().cqr2_autotune(m, n, precision, C.byref(res)), "cqr2_autotune")
+    return {"gram_ctas": res.gram_ctas, "fused": bool(res.fused), "ms": res.ms, "candidates": res.candidates}
+
+
+def cqr2_tune_set_small_limit(limit: int) -> None:
+    N.check(N.load().cqr2_tune_set_small_limit(int(limit)), "cqr2_tune_set_small_limit")
+
+
+def cqr2_tune_table() -> str:
+    lib = N.load()
+    size = int(lib.cqr2_tune_table(None, 0))
+    buf = C.create_string_buffer(size)
+    lib.cqr2_tune_table(buf, size)
+    return buf.value.decode()
+
+
+class Batch:
+    """Many independent CholeskyQR2 factorizations per call (cqr2_batch_*)."""
+
+    def __init__(self, max_count: int, precision: int = CQR2_FP64, small_work_limit: int | None = None,
+                 streams: int | None = None, fused: bool = True, stream=None):
+        cfg = None
+        if small_work_limit is not None or streams is not None:
+            cfg = N.BatchConfig(int(small_work_limit if small_work_limit is not None else 32768 * 64 * 64),
+                                int(streams or 4), 1 if fused else 0)
+        h = C.c_void_p()
+        N.check(N.load().cqr2_batch_create(C.byref(h), int(max_count), precision,
+                                           C.byref(cfg) if cfg is not None else None, _stream_handle(stream)),
+                "cqr2_batch_create")
+        self.handle = h
+        self.max_count = int(max_count)
+
+    def factor(self, problems, sync: bool = True):
+        """problems: list of (A, Q, R) column-major CUDA float64 tensors.
+        Returns a list of Info (sync=True) or None."""
+        k = len(problems)
+        arr = (N.Problem * max(k, 1))()
+        for i, (A, Q, R) in enumerate(problems):
+            m, n = A.shape
+            a, lda = _mat(A, m, n, "A")
+            q, ldq = _mat(Q, m, n, "Q")
+            r, ldr = _mat(R, n, n, "R")
+            arr[i] = N.Problem(m, n, a, lda, q, ldq, r, ldr)
+        infos = (Info * max(k, 1))() if sync else None
+        st = N.load().cqr2_batch_factor(self.handle, arr, k, infos)
+        if st not in (CQR2_OK, CQR2_ERR_NOT_SPD):
+            N.check(st, "cqr2_batch_factor")
+        return list(infos)[:k] if sync else None
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            N.load().cqr2_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 # ------------------------------------------------------------ helpers
 
 class Plan:
     """Owns a cqr2 plan for m x n factorizations on the current device."""
 
-    def __init__(self, m: int, n: int, precision: int = CQR2_FP64, fused: bool = False, stream=None):
+    def __init__(self, m: int, n: int, precision: int = CQR2_FP64, fused: bool = False, stream=None,
+                 graph: bool = False):
         self.m, self.n = int(m), int(n)
-        self.handle = cqr2_plan_create(self.m, self.n, precision, CQR2_FUSED if fused else 0, stream)
+        flags = (CQR2_FUSED if fused else 0) | (N.CQR2_GRAPH if graph else 0)
+        self.handle = cqr2_plan_create(self.m, self.n, precision, flags, stream)
+
+    def factor_rows(self, A, Q=None, R=None, sync: bool = True):
+        """Factor an m-row matrix with n <= m <= the plan's m."""
+        m = A.shape[0]
+        if Q is None:
+            Q = empty_colmajor(m, self.n, device=A.device)
+        if R is None:
+            R = empty_colmajor(self.n, self.n, device=A.device)
+        info = cqr2_factor_rows(self.handle, m, self.n, A, Q, R, sync)
+        return Q, R, info
+
+    def lstsq_rows(self, A, b, Q=None, R=None, x=None, sync: bool = True):
+        torch = _torch()
+        m = A.shape[0]
+        if Q is None:
+            Q = empty_colmajor(m, self.n, device=A.device)
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=A.device)
+        info = cqr2_lstsq_rows(self.handle, m, self.n, A, b, x, Q, R, sync)
+        return x, info
+
+    def set_gram_ctas(self, ctas_per_sm: int) -> None:
+        cqr2_plan_set_gram_ctas(self.handle, ctas_per_sm)
+
+    def set_fused(self, fused: bool) -> None:
+        cqr2_plan_set_fused(self.handle, fused)
 
     def set_stream(self, stream) -> None:
         N.check(N.load().cqr2_plan_set_stream(self.handle, _stream_handle(stream)), "cqr2_plan_set_stream")

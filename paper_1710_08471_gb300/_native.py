@@ -23,6 +23,7 @@ CQR2_FP64 = 0
 CQR2_OZAKI_BF16 = 1
 CQR2_OZAKI_BF16_S6 = 2
 CQR2_FUSED = 0x1
+CQR2_GRAPH = 0x2
 CQR2_NUM_STAGES = 11
 
 
@@ -30,6 +31,22 @@ class Info(C.Structure):
     """cqr2_info_t"""
     _fields_ = [("status", C.c_int32), ("failed_pass", C.c_int32), ("failed_pivot", C.c_int64),
                 ("pivot_value", C.c_double)]
+
+
+class Problem(C.Structure):
+    """cqr2_problem_t"""
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64), ("Q", C.c_void_p),
+                ("ldq", C.c_int64), ("R", C.c_void_p), ("ldr", C.c_int64)]
+
+
+class BatchConfig(C.Structure):
+    """cqr2_batch_config_t"""
+    _fields_ = [("small_work_limit", C.c_int64), ("streams", C.c_int32), ("fused", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    """cqr2_tune_result_t"""
+    _fields_ = [("gram_ctas", C.c_int32), ("fused", C.c_int32), ("ms", C.c_double), ("candidates", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -44,7 +61,17 @@ SIGNATURES = {
     "cqr2_plan_destroy": (None, [_P]),
     "cqr2_factor": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_lstsq": (C.c_int, [_P, _D, _I64, _D, _D, _D, _I64, _D, _I64, C.POINTER(Info)]),
+    "cqr2_factor_rows": (C.c_int, [_P, _I64, _D, _I64, _D, _I64, _D, _I64, C.POINTER(Info)]),
+    "cqr2_lstsq_rows": (C.c_int, [_P, _I64, _D, _I64, _D, _D, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_plan_info": (C.c_int, [_P, C.POINTER(Info)]),
+    "cqr2_plan_set_gram_ctas": (C.c_int, [_P, C.c_int32]),
+    "cqr2_plan_set_fused": (C.c_int, [_P, C.c_int32]),
+    "cqr2_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(BatchConfig), _P]),
+    "cqr2_batch_factor": (C.c_int, [_P, C.POINTER(Problem), C.c_int32, C.POINTER(Info)]),
+    "cqr2_batch_destroy": (None, [_P]),
+    "cqr2_autotune": (C.c_int, [_I64, _I64, C.c_int32, C.POINTER(TuneResult)]),
+    "cqr2_tune_set_small_limit": (C.c_int, [_I64]),
+    "cqr2_tune_table": (C.c_int64, [C.c_char_p, _I64]),
     "cqr2_syrk": (C.c_int, [_P, _D, _I64, _D, _I64]),
     "cqr2_cholinv": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_qform": (C.c_int, [_P, _D, _I64, _D, _I64, _D, _I64]),

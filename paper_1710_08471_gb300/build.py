@@ -21,7 +21,8 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(LIBDIR, "libcqr2.so")
 
-SOURCES = ["api.cu", "gram.cu", "qform.cu", "gemm.cu", "cholinv.cu", "lstsq.cu", "ozaki.cu"]
+SOURCES = ["api.cu", "gram.cu", "qform.cu", "gemm.cu", "cholinv.cu", "lstsq.cu", "ozaki.cu", "batched.cu",
+           "batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

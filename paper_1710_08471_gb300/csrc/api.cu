@@ -18,7 +18,9 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace cqr2
 
 struct cqr2_plan_st {
-  int64_t m = 0, n = 0;
+  int64_t m = 0, n = 0;  // m is the largest row count the plan serves
+  int64_t cm = 0;        // row count of the call in progress (geometry below is for cm)
+  int gram_cps = 4;      // Gram CTAs per SM (autotuned knob, 1..GRAM_CPS_MAX)
   int precision = CQR2_FP64;
   unsigned flags = 0;
   int device = 0;
@@ -57,6 +59,15 @@ struct cqr2_plan_st {
   int* oz_fexp = nullptr;
   double* oz_partial = nullptr;
   OzMaps oz_maps;
+  // CUDA graph of the last factorization (CQR2_GRAPH), keyed by its arguments
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct {
+    const void* A;
+    void* Q;
+    void* R;
+    int64_t lda, ldq, ldr, m;
+  } gkey{};
   // per-stage CUDA-event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -65,6 +76,8 @@ struct cqr2_plan_st {
 };
 
 namespace {
+
+constexpr int GRAM_CPS_MAX = 8;
 
 #define TRY(call)                             \
   do {                                        \
@@ -120,12 +133,34 @@ cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   return (cqr2_status_t)info->status;
 }
 
+}  // namespace
+
+cudaError_t cqr2::plan_status_copy(cqr2_plan_st* p, DevStatus* dst, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, p->st, sizeof(DevStatus), cudaMemcpyDeviceToDevice, s);
+}
+
+namespace {
+
+// Prepares the plan's launch geometry for an m-row call (m <= plan m).
+cqr2_status_t set_rows(cqr2_plan_st* p, int64_t m) {
+  if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
+  if (m == p->cm) return CQR2_OK;
+  p->g = gram_geometry(m, (int)p->n, 0, p->gram_cps);
+  p->gemv_nsplit = gemv_splits(m, (int)p->n);
+  if (p->oz_S && ozaki_make_maps(p->oz_maps, m, (int)p->n, p->oz_S, p->oz_planes, p->oz_rinv) != cudaSuccess) {
+    p->cm = 0;
+    return CQR2_ERR_CUDA;
+  }
+  p->cm = m;
+  return CQR2_OK;
+}
+
 // Split-precision CholeskyQR2: the Gram and Q-forming contractions on the
 // BF16 tensor cores (Ozaki slices), CholInv and R2 R1 in native FP64.
 cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
                                 int64_t ldr) {
   const int n = (int)p->n, S = p->oz_S;
-  const int64_t m = p->m;
+  const int64_t m = p->cm;
   cudaStream_t s = p->stream;
   TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   for (int pass = 1; pass <= 2; ++pass) {
@@ -173,7 +208,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   // ---- pass 1: W1 = A^T A, [L1, Y1] = CholInv(W1)
   {
     Stage st(p, CQR2_STAGE_GRAM1);
-    TRY(gram_partials(dA, lda, p->m, n, p->g, p->partial, s));
+    TRY(gram_partials(dA, lda, p->cm, n, p->g, p->partial, s));
     TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
   }
   {
@@ -189,19 +224,19 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
     TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
     if (p->fused) {
       // Q1 and the partial Grams of Q1 in one sweep over A
-      TRY(qform_gram_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->g, p->partial, s));
+      TRY(qform_gram_small(dA, lda, p->cm, n, p->Rp, dQ, ldq, p->g, p->partial, s));
     } else {
-      TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, s));
+      TRY(qform_small(dA, lda, p->cm, n, p->Rp, dQ, ldq, s));
     }
   } else {
     Stage st(p, CQR2_STAGE_QFORM1);
-    TRY(gemm_f64(p->m, n, n, 1.0, dA, lda, p->Y, n, 0.0, p->Q1, p->m, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    TRY(gemm_f64(p->cm, n, n, 1.0, dA, lda, p->Y, n, 0.0, p->Q1, p->m, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
     X2 = p->Q1;
     ldx2 = p->m;
   }
   {
     Stage st(p, CQR2_STAGE_GRAM2);
-    if (!p->fused) TRY(gram_partials(X2, ldx2, p->m, n, p->g, p->partial, s));
+    if (!p->fused) TRY(gram_partials(X2, ldx2, p->cm, n, p->g, p->partial, s));
     TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
   }
   {
@@ -212,9 +247,9 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
     Stage st(p, CQR2_STAGE_QFORM2);
     if (p->small) {
       TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
-      TRY(qform_small(dQ, ldq, p->m, n, p->Rp, dQ, ldq, s));  // in place, panel by panel
+      TRY(qform_small(dQ, ldq, p->cm, n, p->Rp, dQ, ldq, s));  // in place, panel by panel
     } else {
-      TRY(gemm_f64(p->m, n, n, 1.0, X2, ldx2, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+      TRY(gemm_f64(p->cm, n, n, 1.0, X2, ldx2, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
     }
   }
   // ---- R = R2 R1 with R2 = L2^T
@@ -256,7 +291,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (n < 1 || m < n || n > 65535) return CQR2_ERR_INVALID_ARG;
   if (precision != CQR2_FP64 && precision != CQR2_OZAKI_BF16 && precision != CQR2_OZAKI_BF16_S6)
     return CQR2_ERR_INVALID_ARG;
-  if (flags & ~CQR2_FUSED) return CQR2_ERR_INVALID_ARG;
+  if (flags & ~(CQR2_FUSED | CQR2_GRAPH)) return CQR2_ERR_INVALID_ARG;
   const int oz_S = precision == CQR2_OZAKI_BF16 ? 7 : (precision == CQR2_OZAKI_BF16_S6 ? 6 : 0);
   if (oz_S && !ozaki_supported((int)n, oz_S)) return CQR2_ERR_UNSUPPORTED;
   int dev = 0;
@@ -269,7 +304,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->flags = flags;
   p->device = dev;
   p->stream = static_cast<cudaStream_t>(stream);
-  p->g = gram_geometry(m, (int)n, 0);
+  p->g = gram_geometry(m, (int)n, 0, GRAM_CPS_MAX);  // size the partials for the largest split
   p->small = qform_group_width((int)n) > 0;
   p->fused = (flags & CQR2_FUSED) && qform_gram_fusable((int)n);
   p->gemv_nsplit = gemv_splits(m, (int)n);
@@ -353,6 +388,8 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
       return CQR2_ERR_CUDA;
     }
   }
+  p->g = gram_geometry(m, (int)n, 0, p->gram_cps);
+  p->cm = m;  // geometry and tensor maps above are for the full row count
   std::memset(p->h_st, 0, sizeof(DevStatus));
   if (cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream) != cudaSuccess) {
     cudaFreeHost(p->h_st);
@@ -376,6 +413,8 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
   if (!plan) return;
   cudaStreamSynchronize(plan->stream);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
   cudaFree(plan->hA_dev);
   cudaFree(plan->hQ_dev);
   cudaFree(plan->hR_dev);
@@ -389,32 +428,104 @@ cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info) {
   return read_info(plan, info);
 }
 
-cqr2_status_t cqr2_factor(cqr2_plan_t p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
-                          int64_t ldr, cqr2_info_t* info) {
+cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64_t lda, double* dQ, int64_t ldq,
+                               double* dR, int64_t ldr, cqr2_info_t* info) {
   if (!p || !dA || !dQ || !dR) return CQR2_ERR_INVALID_ARG;
-  if (bad_ld(lda, p->m) || bad_ld(ldq, p->m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
+  if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, m) || bad_ld(ldq, m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
   if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
-  if ((r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) return r;
+  if ((r = set_rows(p, m)) != CQR2_OK) return r;
+  if ((p->flags & CQR2_GRAPH) && p->stream && !p->profiling) {
+    // Replay the captured launch sequence when the arguments repeat;
+    // otherwise capture this call's sequence into a new graph first.
+    const bool same = p->gexec && p->gkey.A == dA && p->gkey.Q == dQ && p->gkey.R == dR && p->gkey.lda == lda &&
+                      p->gkey.ldq == ldq && p->gkey.ldr == ldr && p->gkey.m == m;
+    if (!same) {
+      if (p->gexec) cudaGraphExecDestroy(p->gexec);
+      if (p->graph) cudaGraphDestroy(p->graph);
+      p->gexec = nullptr;
+      p->graph = nullptr;
+      TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+      r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
+      if (r != CQR2_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return r != CQR2_OK ? r : CQR2_ERR_CUDA;
+      }
+      if (cudaGraphInstantiate(&p->gexec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        p->gexec = nullptr;
+        return CQR2_ERR_CUDA;
+      }
+      p->graph = g;
+      p->gkey.A = dA;
+      p->gkey.Q = dQ;
+      p->gkey.R = dR;
+      p->gkey.lda = lda;
+      p->gkey.ldq = ldq;
+      p->gkey.ldr = ldr;
+      p->gkey.m = m;
+    }
+    TRY(cudaGraphLaunch(p->gexec, p->stream));
+  } else if ((r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) {
+    return r;
+  }
   if (info) return read_info(p, info);
   return CQR2_OK;
 }
 
+cqr2_status_t cqr2_plan_set_gram_ctas(cqr2_plan_t p, int32_t ctas_per_sm) {
+  if (!p || ctas_per_sm < 1 || ctas_per_sm > GRAM_CPS_MAX) return CQR2_ERR_INVALID_ARG;
+  p->gram_cps = ctas_per_sm;
+  p->cm = 0;  // recompute the geometry on the next call
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t p, int32_t fused) {
+  if (!p) return CQR2_ERR_INVALID_ARG;
+  p->fused = fused && !p->oz_S && qform_gram_fusable((int)p->n) && p->small;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_factor(cqr2_plan_t p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                          int64_t ldr, cqr2_info_t* info) {
+  if (!p) return CQR2_ERR_INVALID_ARG;
+  return cqr2_factor_rows(p, p->m, dA, lda, dQ, ldq, dR, ldr, info);
+}
+
 cqr2_status_t cqr2_lstsq(cqr2_plan_t p, const double* dA, int64_t lda, const double* db, double* dx, double* dQ,
                          int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info) {
+  if (!p) return CQR2_ERR_INVALID_ARG;
+  return cqr2_lstsq_rows(p, p->m, dA, lda, db, dx, dQ, ldq, dR, ldr, info);
+}
+
+cqr2_status_t cqr2_lstsq_rows(cqr2_plan_t p, int64_t m, const double* dA, int64_t lda, const double* db, double* dx,
+                              double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info) {
   if (!p || !dA || !db || !dx || !dQ) return CQR2_ERR_INVALID_ARG;
-  if (bad_ld(lda, p->m) || bad_ld(ldq, p->m)) return CQR2_ERR_INVALID_ARG;
+  if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, m) || bad_ld(ldq, m)) return CQR2_ERR_INVALID_ARG;
   if (dR && bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
   if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if ((r = set_rows(p, m)) != CQR2_OK) return r;
   double* R = dR ? dR : p->Rf;
   const int64_t ldR = dR ? ldr : p->n;
   if ((r = factor_impl(p, dA, lda, dQ, ldq, R, ldR)) != CQR2_OK) return r;
   {
     Stage st(p, CQR2_STAGE_LSTSQ);
-    TRY(gemv_t_partials(dQ, ldq, p->m, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
+    TRY(gemv_t_partials(dQ, ldq, p->cm, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
     TRY(lstsq_solve(p->lspart, p->gemv_nsplit, (int)p->n, R, ldR, dx, p->stream));
   }
   if (info) return read_info(p, info);
@@ -425,15 +536,16 @@ cqr2_status_t cqr2_syrk(cqr2_plan_t p, const double* dA, int64_t lda, double* dW
   if (!p || !dA || !dW || bad_ld(lda, p->m) || bad_ld(ldw, p->n)) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if ((r = set_rows(p, p->m)) != CQR2_OK) return r;
   if (p->oz_S) {
     const int n = (int)p->n;
     TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
-    TRY(ozaki_colmax(dA, lda, p->m, n, p->oz_colmax, p->oz_cexp, p->stream));
-    TRY(ozaki_slice_cols(dA, lda, p->m, n, p->oz_S, p->oz_cexp, p->oz_planes, p->stream));
-    TRY(ozaki_gram(p->oz_maps, p->m, n, p->oz_S, p->oz_cexp, p->oz_partial, dW, ldw, p->st, p->stream));
+    TRY(ozaki_colmax(dA, lda, p->cm, n, p->oz_colmax, p->oz_cexp, p->stream));
+    TRY(ozaki_slice_cols(dA, lda, p->cm, n, p->oz_S, p->oz_cexp, p->oz_planes, p->stream));
+    TRY(ozaki_gram(p->oz_maps, p->cm, n, p->oz_S, p->oz_cexp, p->oz_partial, dW, ldw, p->st, p->stream));
     return CQR2_OK;
   }
-  TRY(gram_partials(dA, lda, p->m, (int)p->n, p->g, p->partial, p->stream));
+  TRY(gram_partials(dA, lda, p->cm, (int)p->n, p->g, p->partial, p->stream));
   TRY(gram_reduce(p->partial, p->g, (int)p->n, dW, ldw, p->stream));
   return CQR2_OK;
 }
@@ -457,17 +569,18 @@ cqr2_status_t cqr2_qform(cqr2_plan_t p, const double* dA, int64_t lda, const dou
   if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if ((r = set_rows(p, p->m)) != CQR2_OK) return r;
   const int n = (int)p->n;
   if (p->oz_S) {
     TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
     TRY(ozaki_slice_rinv(dRinv, ldri, n, p->oz_S, true, p->oz_rinv, p->oz_fexp, p->stream));
-    TRY(ozaki_slice_rows(dA, lda, p->m, n, p->oz_S, p->oz_planes, p->oz_rexp, p->stream));
-    TRY(ozaki_qform(p->oz_maps, p->m, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, p->stream));
+    TRY(ozaki_slice_rows(dA, lda, p->cm, n, p->oz_S, p->oz_planes, p->oz_rexp, p->stream));
+    TRY(ozaki_qform(p->oz_maps, p->cm, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, p->stream));
   } else if (p->small) {
     TRY(pack_rinv_from_upper(dRinv, ldri, n, p->Rp, p->stream));
-    TRY(qform_small(dA, lda, p->m, n, p->Rp, dQ, ldq, p->stream));
+    TRY(qform_small(dA, lda, p->cm, n, p->Rp, dQ, ldq, p->stream));
   } else {
-    TRY(gemm_f64(p->m, n, n, 1.0, dA, lda, dRinv, ldri, 0.0, dQ, ldq, GEMM_B_UPPER | GEMM_BETA0, p->stream));
+    TRY(gemm_f64(p->cm, n, n, 1.0, dA, lda, dRinv, ldri, 0.0, dQ, ldq, GEMM_B_UPPER | GEMM_BETA0, p->stream));
   }
   return CQR2_OK;
 }
@@ -524,6 +637,7 @@ cqr2_status_t cqr2_factor_host(cqr2_plan_t p, const double* hA, int64_t lda, dou
   if (bad_ld(lda, p->m) || bad_ld(ldq, p->m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if ((r = set_rows(p, p->m)) != CQR2_OK) return r;
   const size_t mn = (size_t)p->m * p->n * sizeof(double);
   if (!p->hA_dev) {
     if (cudaMalloc(&p->hA_dev, mn) != cudaSuccess || cudaMalloc(&p->hQ_dev, mn) != cudaSuccess ||

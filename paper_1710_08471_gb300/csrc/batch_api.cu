@@ -1,0 +1,366 @@
+// C ABI for many independent factorizations and for the autotuner.
+//
+// cqr2_batch_factor routes every problem of a batch:
+//   * small ones (n <= 64 and m n^2 at most the tuned limit) go to one launch
+//     of the persistent grouped kernel, which factors a whole problem per CTA
+//     from a device work queue, largest first;
+//   * the others run on per-(n, stream) plans spread over several streams
+//     that fork from and join back into the batch's stream, so their kernels
+//     overlap on the device.
+// cqr2_autotune times candidate configurations on the device and keeps the
+// fastest per (n, m bucket, precision) in a process-wide table.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cqr2.h"
+#include "kernels.h"
+
+using namespace cqr2;
+
+struct cqr2_batch_st {
+  int device = 0;
+  int precision = CQR2_FP64;
+  cudaStream_t stream = nullptr;
+  int32_t max_count = 0;
+  cqr2_batch_config_t cfg{};
+  BatchProblem* d_probs = nullptr;
+  BatchStatus* d_status = nullptr;
+  int* d_next = nullptr;
+  BatchProblem* h_probs = nullptr;
+  BatchStatus* h_status = nullptr;
+  DevStatus* d_lstatus = nullptr;  // status words of the planned problems
+  DevStatus* h_lstatus = nullptr;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  struct PlanSlot {
+    cqr2_plan_t plan = nullptr;
+    int64_t m_max = 0;
+  };
+  std::map<std::pair<int64_t, int>, PlanSlot> plans;  // (n, side stream) -> plan
+};
+
+namespace {
+
+struct TuneEntry {
+  int32_t gram_ctas;
+  int32_t fused;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;  // key "n:mbucket:precision"
+int64_t g_small_limit = -1;                 // tuned grouped-kernel limit on m n^2 (-1 = default)
+
+std::string tune_key(int64_t m, int64_t n, int precision) {
+  const int mb = (int)std::floor(std::log2((double)std::max<int64_t>(m, 1)));
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "%lld:%d:%d", (long long)n, mb, precision);
+  return buf;
+}
+
+constexpr int64_t DEFAULT_SMALL_LIMIT = (int64_t)32768 * 64 * 64;
+
+bool lookup_tune(int64_t m, int64_t n, int precision, TuneEntry* e) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(m, n, precision));
+  if (it == g_tune.end()) return false;
+  *e = it->second;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+cqr2_status_t cqr2_batch_create(cqr2_batch_t* batch, int32_t max_count, int32_t precision,
+                                const cqr2_batch_config_t* cfg, void* stream) {
+  if (!batch) return CQR2_ERR_INVALID_ARG;
+  *batch = nullptr;
+  if (max_count < 1) return CQR2_ERR_INVALID_ARG;
+  if (precision != CQR2_FP64 && precision != CQR2_OZAKI_BF16 && precision != CQR2_OZAKI_BF16_S6)
+    return CQR2_ERR_INVALID_ARG;
+  auto* b = new (std::nothrow) cqr2_batch_st();
+  if (!b) return CQR2_ERR_OOM;
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    delete b;
+    return CQR2_ERR_CUDA;
+  }
+  b->precision = precision;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->max_count = max_count;
+  if (cfg) {
+    b->cfg = *cfg;
+  } else {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    b->cfg.small_work_limit = g_small_limit >= 0 ? g_small_limit : DEFAULT_SMALL_LIMIT;
+    b->cfg.streams = 4;
+    b->cfg.fused = 1;
+  }
+  b->cfg.streams = std::max(1, std::min(16, (int)b->cfg.streams));
+  bool ok = cudaMalloc(&b->d_probs, sizeof(BatchProblem) * max_count) == cudaSuccess &&
+            cudaMalloc(&b->d_status, sizeof(BatchStatus) * max_count) == cudaSuccess &&
+            cudaMalloc(&b->d_next, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&b->h_probs, sizeof(BatchProblem) * max_count) == cudaSuccess &&
+            cudaMallocHost(&b->h_status, sizeof(BatchStatus) * max_count) == cudaSuccess &&
+            cudaMalloc(&b->d_lstatus, sizeof(DevStatus) * max_count) == cudaSuccess &&
+            cudaMallocHost(&b->h_lstatus, sizeof(DevStatus) * max_count) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < b->cfg.streams; ++i) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+      b->side.push_back(s);
+      b->joins.push_back(e);
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();
+    cqr2_batch_destroy(b);
+    return CQR2_ERR_OOM;
+  }
+  *batch = b;
+  return CQR2_OK;
+}
+
+void cqr2_batch_destroy(cqr2_batch_t b) {
+  if (!b) return;
+  if (b->stream || true) cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->plans) cqr2_plan_destroy(kv.second.plan);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  cudaFree(b->d_probs);
+  cudaFree(b->d_status);
+  cudaFree(b->d_next);
+  cudaFreeHost(b->h_probs);
+  cudaFreeHost(b->h_status);
+  cudaFree(b->d_lstatus);
+  cudaFreeHost(b->h_lstatus);
+  delete b;
+}
+
+cqr2_status_t cqr2_batch_factor(cqr2_batch_t b, const cqr2_problem_t* problems, int32_t count, cqr2_info_t* infos) {
+  if (!b || (!problems && count > 0) || count < 0 || count > b->max_count) return CQR2_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CQR2_ERR_CUDA;
+  if (dev != b->device) return CQR2_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const cqr2_problem_t& q = problems[i];
+    if (q.n < 1 || q.m < q.n || !q.A || !q.Q || !q.R || q.lda < q.m || q.ldq < q.m || q.ldr < q.n ||
+        (const void*)q.A == (const void*)q.Q)
+      return CQR2_ERR_INVALID_ARG;
+  }
+  // route
+  std::vector<int> small, large;
+  for (int i = 0; i < count; ++i) {
+    const cqr2_problem_t& q = problems[i];
+    const bool is_small = q.n <= BATCH_SMALL_MAX_N && (double)q.m * q.n * q.n <= (double)b->cfg.small_work_limit;
+    (is_small ? small : large).push_back(i);
+  }
+  std::sort(small.begin(), small.end(), [&](int a, int c) {
+    return (double)problems[a].m * problems[a].n * problems[a].n > (double)problems[c].m * problems[c].n * problems[c].n;
+  });
+  // grouped launch for the small problems (on the batch stream)
+  if (!small.empty()) {
+    for (size_t k = 0; k < small.size(); ++k) {
+      const cqr2_problem_t& q = problems[small[k]];
+      b->h_probs[k] = BatchProblem{q.m, q.n, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr};
+    }
+    if (cudaMemcpyAsync(b->d_probs, b->h_probs, sizeof(BatchProblem) * small.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+    if (cqr2_small_batched(b->d_probs, (int)small.size(), b->d_next, b->d_status, b->stream) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+  }
+  // the others: plans on side streams forked from the batch stream
+  std::vector<std::pair<int, cqr2_plan_t>> used;
+  if (!large.empty()) {
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+    const int ns = (int)std::min<size_t>(b->side.size(), large.size());
+    for (int s = 0; s < ns; ++s)
+      if (cudaStreamWaitEvent(b->side[s], b->fork, 0) != cudaSuccess) return CQR2_ERR_CUDA;
+    for (size_t k = 0; k < large.size(); ++k) {
+      const cqr2_problem_t& q = problems[large[k]];
+      const int s = (int)(k % ns);
+      auto& slot = b->plans[{q.n, s}];
+      if (!slot.plan || slot.m_max < q.m) {
+        if (slot.plan) {
+          cudaStreamSynchronize(b->side[s]);
+          cqr2_plan_destroy(slot.plan);
+          slot.plan = nullptr;
+        }
+        const int64_t mm = std::max<int64_t>(q.m, slot.m_max);
+        int prec = b->precision;
+        if (prec != CQR2_FP64 && q.n > OZAKI_MAX_N) prec = CQR2_FP64;
+        cqr2_status_t r = cqr2_plan_create(&slot.plan, mm, q.n, prec, b->cfg.fused ? CQR2_FUSED : 0, b->side[s]);
+        if (r != CQR2_OK) return r;
+        slot.m_max = mm;
+        TuneEntry te;
+        if (lookup_tune(q.m, q.n, prec, &te)) {
+          cqr2_plan_set_gram_ctas(slot.plan, te.gram_ctas);
+          cqr2_plan_set_fused(slot.plan, te.fused);
+        }
+      }
+      cqr2_status_t r = cqr2_factor_rows(slot.plan, q.m, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr, nullptr);
+      if (r != CQR2_OK) return r;
+      if (plan_status_copy(slot.plan, b->d_lstatus + used.size(), b->side[s]) != cudaSuccess) return CQR2_ERR_CUDA;
+      used.push_back({large[k], slot.plan});
+    }
+    for (int s = 0; s < ns; ++s) {
+      if (cudaEventRecord(b->joins[s], b->side[s]) != cudaSuccess) return CQR2_ERR_CUDA;
+      if (cudaStreamWaitEvent(b->stream, b->joins[s], 0) != cudaSuccess) return CQR2_ERR_CUDA;
+    }
+  }
+  if (!infos) return CQR2_OK;
+  // outcome per problem (synchronizes)
+  cqr2_status_t worst = CQR2_OK;
+  if (!small.empty()) {
+    if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * small.size(), cudaMemcpyDeviceToHost,
+                        b->stream) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+  for (size_t k = 0; k < small.size(); ++k) {
+    cqr2_info_t& in = infos[small[k]];
+    const BatchStatus& st = b->h_status[k];
+    in.status = st.failed_pass ? CQR2_ERR_NOT_SPD : CQR2_OK;
+    in.failed_pass = st.failed_pass;
+    in.failed_pivot = st.failed_pass ? st.failed_pivot : -1;
+    in.pivot_value = 0.0;
+    if (st.failed_pass) worst = CQR2_ERR_NOT_SPD;
+  }
+  // Each planned problem's status word was copied out right after its call.
+  if (!used.empty()) {
+    if (cudaMemcpy(b->h_lstatus, b->d_lstatus, sizeof(DevStatus) * used.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return CQR2_ERR_CUDA;
+  }
+  for (size_t k = 0; k < used.size(); ++k) {
+    cqr2_info_t& in = infos[used[k].first];
+    const DevStatus& st = b->h_lstatus[k];
+    in.status = st.status == 0 ? CQR2_OK : (st.status == 5 ? CQR2_ERR_TIMEOUT : CQR2_ERR_NOT_SPD);
+    in.failed_pass = st.status == 2 ? st.pass : 0;
+    in.failed_pivot = st.status == 2 ? st.pivot : -1;
+    in.pivot_value = st.status == 2 ? st.value : 0.0;
+    if (in.status != CQR2_OK) worst = (cqr2_status_t)in.status;
+  }
+  return worst;
+}
+
+cqr2_status_t cqr2_autotune(int64_t m, int64_t n, int32_t precision, cqr2_tune_result_t* out) {
+  if (n < 1 || m < n || !out) return CQR2_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  double* A = nullptr;
+  double* Q = nullptr;
+  double* R = nullptr;
+  const size_t mn = (size_t)m * n * sizeof(double);
+  if (cudaMalloc(&A, mn) != cudaSuccess || cudaMalloc(&Q, mn) != cudaSuccess ||
+      cudaMalloc(&R, (size_t)n * n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(A);
+    cudaFree(Q);
+    return CQR2_ERR_OOM;
+  }
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return CQR2_ERR_CUDA;
+  // A well-conditioned scratch matrix: columns of the identity pattern plus a
+  // smooth fill (the timings do not depend on the values).
+  if (cudaMemsetAsync(A, 0, mn, s) != cudaSuccess) return CQR2_ERR_CUDA;
+  for (int64_t j = 0; j < n; ++j) {
+    const double one = 1.0;
+    if (cudaMemcpyAsync(A + j + j * m, &one, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cqr2_plan_t plan = nullptr;
+  cqr2_status_t r = cqr2_plan_create(&plan, m, n, precision, CQR2_FUSED, s);
+  if (r != CQR2_OK) {
+    cudaStreamDestroy(s);
+    cudaFree(A);
+    cudaFree(Q);
+    cudaFree(R);
+    return r;
+  }
+  const int cps_list[] = {1, 2, 4, 8};
+  const int fused_list[] = {0, 1};
+  double best = 1e30;
+  TuneEntry bestE{4, 1, 0.0};
+  int tried = 0;
+  for (int f : fused_list) {
+    if (f && (precision != CQR2_FP64 || n > 128)) continue;
+    for (int cps : cps_list) {
+      cqr2_plan_set_fused(plan, f);
+      cqr2_plan_set_gram_ctas(plan, cps);
+      cqr2_factor(plan, A, m, Q, m, R, n, nullptr);  // warm
+      cudaEventRecord(e0, s);
+      const int reps = 3;
+      for (int i = 0; i < reps; ++i) cqr2_factor(plan, A, m, Q, m, R, n, nullptr);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      ++tried;
+      if (ms < best) {
+        best = ms;
+        bestE = TuneEntry{cps, f, ms};
+      }
+    }
+  }
+  cqr2_plan_destroy(plan);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaFree(A);
+  cudaFree(Q);
+  cudaFree(R);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(m, n, precision)] = bestE;
+  }
+  out->gram_ctas = bestE.gram_ctas;
+  out->fused = bestE.fused;
+  out->ms = bestE.ms;
+  out->candidates = tried;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_tune_set_small_limit(int64_t limit) {
+  if (limit < 0) return CQR2_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_small_limit = limit;
+  return CQR2_OK;
+}
+
+int64_t cqr2_tune_table(char* buf, int64_t size) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string s;
+  char line[160];
+  for (auto& kv : g_tune) {
+    std::snprintf(line, sizeof(line), "%s gram_ctas=%d fused=%d ms=%.4f\n", kv.first.c_str(), kv.second.gram_ctas,
+                  kv.second.fused, kv.second.ms);
+    s += line;
+  }
+  std::snprintf(line, sizeof(line), "small_work_limit=%lld\n",
+                (long long)(g_small_limit >= 0 ? g_small_limit : DEFAULT_SMALL_LIMIT));
+  s += line;
+  if (buf && size > 0) {
+    const size_t k = std::min<size_t>((size_t)size - 1, s.size());
+    std::memcpy(buf, s.data(), k);
+    buf[k] = 0;
+  }
+  return (int64_t)s.size() + 1;
+}
+
+}  // extern "C"

@@ -199,7 +199,7 @@ cudaError_t launch_tile(const double* A, int64_t lda, int64_t m, int n, const Gr
 
 }  // namespace
 
-GramGeom gram_geometry(int64_t m, int n, int64_t max_splits) {
+GramGeom gram_geometry(int64_t m, int n, int64_t max_splits, int ctas_per_sm) {
   GramGeom g;
   g.T = n <= 32 ? 32 : (n <= 64 ? 64 : 128);
   g.ntile = (int)ceil_div(n, g.T);
@@ -207,8 +207,8 @@ GramGeom gram_geometry(int64_t m, int n, int64_t max_splits) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // About four CTAs per SM in total, but never a range shorter than one chunk.
-  int64_t want = std::max<int64_t>(1, ceil_div((int64_t)4 * sms, g.ntiles_total));
+  // About ctas_per_sm CTAs per SM in total, but never a range shorter than one chunk.
+  int64_t want = std::max<int64_t>(1, ceil_div((int64_t)std::max(1, ctas_per_sm) * sms, g.ntiles_total));
   want = std::min<int64_t>(want, std::max<int64_t>(1, ceil_div(m, KC)));
   if (max_splits > 0) want = std::min<int64_t>(want, max_splits);
   g.rows_per_split = ceil_div(ceil_div(m, want), KC) * KC;

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct cqr2_plan_st;
+
 namespace cqr2 {
 
 // Process-wide count of kernel launches issued by this library.
@@ -25,7 +27,8 @@ struct GramGeom {
   int64_t rows_per_split = 0;
   size_t partial_doubles() const { return (size_t)nsplit * ntiles_total * T * T; }
 };
-GramGeom gram_geometry(int64_t m, int n, int64_t max_splits);
+// ctas_per_sm: target number of Gram CTAs per SM (an autotuned knob).
+GramGeom gram_geometry(int64_t m, int n, int64_t max_splits, int ctas_per_sm = 4);
 cudaError_t gram_partials(const double* A, int64_t lda, int64_t m, int n, const GramGeom& g,
                           double* partial, cudaStream_t s);
 cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double* W, int64_t ldw,
@@ -112,6 +115,29 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
                        int64_t ldw, DevStatus* st, cudaStream_t s);
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* rexp, const int* fexp, double* Q,
                         int64_t ldq, DevStatus* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched
+// One problem of a grouped launch (same layout as cqr2_problem_t).
+struct BatchProblem {
+  int64_t m, n;
+  const double* A;
+  int64_t lda;
+  double* Q;
+  int64_t ldq;
+  double* R;
+  int64_t ldr;
+};
+struct BatchStatus {
+  int failed_pass;   // 0 = ok
+  int failed_pivot;  // -1 = none
+};
+constexpr int BATCH_SMALL_MAX_N = 64;
+// Enqueue a copy of a plan's device status word (outcome of its last call).
+cudaError_t plan_status_copy(struct ::cqr2_plan_st* p, DevStatus* dst, cudaStream_t s);
+size_t batched_small_smem();
+// Persistent grouped kernel: every problem (n <= 64) factored by one CTA.
+cudaError_t cqr2_small_batched(const BatchProblem* probs, int count, int* next, BatchStatus* status,
+                               cudaStream_t s);
 
 // ---------------------------------------------------------------- lstsq
 // c = Q^T b as split-m partials, then x solves R x = c (back substitution).

@@ -396,8 +396,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(const __grid_const
     const int64_t kend = min(p.m, kbase + p.rows_per_split);
     nk = kend > kbase ? (int)((kend - kbase + OZ_BK - 1) / OZ_BK) : 0;
   } else {
-    j0 = (int64_t)OZ_BN * blockIdx.x;
-    i0 = (int64_t)OZ_BM * blockIdx.y;
+    // 1-D grid: the column tiles of one row tile are neighbours, so the A
+    // slices they share are read once from memory and then from L2.
+    const int64_t lin = (int64_t)blockIdx.x;
+    j0 = (int64_t)OZ_BN * (lin % p.ntile_j);
+    i0 = (int64_t)OZ_BM * (lin / p.ntile_j);
     kbase = 0;
     nk = (int)((j0 + OZ_BN + OZ_BK - 1) / OZ_BK);  // R^-1 upper triangular: k < j0 + 64
     const int nkmax = (p.n + OZ_BK - 1) / OZ_BK;
@@ -748,7 +751,8 @@ cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* 
   p.out = Q;
   p.ldo = ldq;
   p.st = st;
-  dim3 grid((unsigned)g.ntile_j, (unsigned)ceil_div(m, OZ_BM));
+  p.ntile_j = g.ntile_j;
+  dim3 grid((unsigned)(g.ntile_j * ceil_div(m, OZ_BM)));
   const CUtensorMap& a = *(const CUtensorMap*)maps.row_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.rinv_b;
   return S == 7 ? launch_oz<7, OZ_QFORM>(a, b, p, grid, s) : launch_oz<6, OZ_QFORM>(a, b, p, grid, s);

@@ -1,0 +1,205 @@
+"""Continuous-batching least-squares server over the CholeskyQR2 C ABI.
+
+Requests (m x n least-squares solves, x = R^-1 Q^T b through CholeskyQR2)
+arrive over time. The server:
+
+* queues arrivals in order;
+* admits the head of the queue when a slot (a CUDA stream with its own
+  plans) is free and the request's device memory -- A, Q, R, b, x -- fits in
+  the HBM budget next to what is already in flight;
+* enqueues the request's copy-in and cqr2_lstsq_rows on the slot's stream, so
+  requests that arrive while others run overlap on the device, and keeps A,
+  Q and R on the device until the request completes;
+* polls completion events, frees the memory, and admits more work.
+
+Plans are created per (slot, n) for the largest m the server accepts and are
+reused for every request of that n (cqr2_lstsq_rows takes the request's m).
+Every computation runs in libcqr2's kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+import paper_1710_08471_gb300 as cq
+from . import _native as N
+
+
+@dataclasses.dataclass
+class Request:
+    id: int
+    t_arrival: float          # seconds since the start of the run
+    m: int
+    n: int
+    A_src: object             # device tensor (m x n, column-major) to copy in
+    b_src: object             # device vector (m)
+    # filled by the server
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    status: int = -1
+    x: object = None
+    R: object = None
+    Q: object = None
+    slot: int = -1
+
+    @property
+    def bytes(self) -> int:
+        return 8 * (2 * self.m * self.n + self.n * self.n + self.m + self.n)
+
+
+class Server:
+    def __init__(self, budget_bytes: float, slots: int = 8, precision: int = cq.CQR2_FP64, m_max: int = 262144,
+                 n_values=(16, 32, 64, 128, 256), keep_outputs: bool = False):
+        import torch
+
+        self.torch = torch
+        self.budget = float(budget_bytes)
+        self.precision = precision
+        self.m_max = int(m_max)
+        self.keep = keep_outputs
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.plans = [dict() for _ in range(slots)]
+        self.busy = [None] * slots  # (request, event)
+        self.inflight_bytes = 0
+        self.workspace_bytes = 0
+        for s in range(slots):
+            for n in n_values:
+                self._plan(s, n)
+
+    def _plan(self, slot: int, n: int):
+        p = self.plans[slot].get(n)
+        if p is None:
+            prec = self.precision if n <= 1024 else cq.CQR2_FP64
+            p = cq.Plan(self.m_max, n, precision=prec, stream=self.streams[slot])
+            self.plans[slot][n] = p
+            self.workspace_bytes += p.workspace_bytes
+        return p
+
+    def _submit(self, r: Request, slot: int, t0: float):
+        torch = self.torch
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            A = cq.empty_colmajor(r.m, r.n, device="cuda")
+            A.copy_(r.A_src)
+            b = r.b_src.clone()
+            Q = cq.empty_colmajor(r.m, r.n, device="cuda")
+            R = cq.empty_colmajor(r.n, r.n, device="cuda")
+            x = torch.empty(r.n, dtype=torch.float64, device="cuda")
+            plan = self._plan(slot, r.n)
+            cq.cqr2_lstsq_rows(plan.handle, r.m, r.n, A, b, x, Q, R, sync=False)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        r.t_admit = time.perf_counter() - t0
+        r.slot = slot
+        # hold the buffers until completion
+        self.busy[slot] = (r, ev, (A, b, Q, R, x), plan)
+        self.inflight_bytes += r.bytes
+
+    def _retire(self, slot: int, t0: float):
+        r, ev, bufs, plan = self.busy[slot]
+        r.t_done = time.perf_counter() - t0
+        info = N.Info()
+        # status word of the plan's last call: the slot's stream has finished it
+        N.load().cqr2_plan_info(plan.handle, info)
+        r.status = info.status
+        A, b, Q, R, x = bufs
+        r.x = x
+        if self.keep:
+            r.Q, r.R = Q, R
+        self.busy[slot] = None
+        self.inflight_bytes -= r.bytes
+
+    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+        """Serve `requests` (sorted by arrival). With realtime, a request is
+        not admitted before its arrival time; otherwise all are available at 0."""
+        queue = collections.deque()
+        pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
+        done = []
+        self.torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slots = len(self.streams)
+        limit = self.budget - self.workspace_bytes
+        while pending or queue or any(b is not None for b in self.busy):
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].t_arrival <= now):
+                queue.append(pending.popleft())
+            for s in range(slots):
+                if self.busy[s] is not None and self.busy[s][1].query():
+                    done.append(self.busy[s][0])
+                    self._retire(s, t0)
+            while queue and queue[0].bytes > limit:
+                # larger than the whole budget: it can never be admitted
+                r = queue.popleft()
+                r.status = N.CQR2_ERR_OOM
+                r.t_done = time.perf_counter() - t0
+                done.append(r)
+            for s in range(slots):
+                if not queue:
+                    break
+                if self.busy[s] is None and self.inflight_bytes + queue[0].bytes <= limit:
+                    self._submit(queue.popleft(), s, t0)
+            if not queue and pending and realtime:
+                # idle until the next arrival
+                wait = pending[0].t_arrival - (time.perf_counter() - t0)
+                if wait > 0 and all(b is None for b in self.busy):
+                    time.sleep(min(wait, 0.001))
+        t_end = time.perf_counter() - t0
+        lat = sorted((r.t_done - r.t_arrival) for r in done) if realtime else sorted(r.t_done for r in done)
+        return {
+            "completed": len(done),
+            "failed": sum(1 for r in done if r.status != 0),
+            "seconds": t_end,
+            "qr_per_s": len(done) / t_end if t_end > 0 else float("nan"),
+            "p50_ms": 1e3 * percentile(lat, 50),
+            "p99_ms": 1e3 * percentile(lat, 99),
+            "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
+            "workspace_bytes": self.workspace_bytes,
+        }
+
+    def close(self):
+        for d in self.plans:
+            for p in d.values():
+                p.close()
+        self.plans = []
+
+
+def percentile(sorted_vals, q: float) -> float:
+    if not sorted_vals:
+        return float("nan")
+    k = (len(sorted_vals) - 1) * q / 100.0
+    f = math.floor(k)
+    c = min(f + 1, len(sorted_vals) - 1)
+    return sorted_vals[f] + (sorted_vals[c] - sorted_vals[f]) * (k - f)
+
+
+class InputPool:
+    """Device-resident synthetic inputs for request streams: for every n and
+    a few condition-number buckets, one m_max x n matrix built by the seeded
+    generator (synth.make_matrix) on the host and copied to the device once; a
+    request of m rows uses the first m rows. The request's kappa is rounded to
+    the nearest bucket (log scale)."""
+
+    def __init__(self, m_max: int, n_values, kappas=(1e1, 1e3, 1e5), seed: int = 100):
+        import numpy as np
+        import torch
+
+        import synth
+
+        self.kappas = list(kappas)
+        self.A = {}
+        for n in n_values:
+            for i, k in enumerate(self.kappas):
+                h = synth.make_matrix(m_max, n, k, seed=seed, mid=1000 * n + i)
+                t = torch.from_numpy(np.ascontiguousarray(h.T)).cuda().t()
+                self.A[(n, i)] = t
+        self.b = torch.from_numpy(synth.make_rhs(m_max, seed=seed)).cuda()
+
+    def bucket(self, kappa: float) -> int:
+        lk = math.log10(max(kappa, 1.0))
+        return min(range(len(self.kappas)), key=lambda i: abs(math.log10(self.kappas[i]) - lk))
+
+    def request(self, rid: int, t: float, m: int, n: int, kappa: float) -> Request:
+        i = self.bucket(kappa)
+        return Request(id=rid, t_arrival=t, m=m, n=n, A_src=self.A[(n, i)][:m], b_src=self.b[:m])

@@ -1,0 +1,158 @@
+"""Variable-m plans, CUDA-graph replay, grouped batches and the autotuner,
+each checked against the CPU FP64 oracle with the FP64 tolerances of
+test_gpu_parity (orthogonality <= 1e-12, residual <= 1e-13, R relative
+<= 1e-12 kappa) and, where a result must not depend on how it was scheduled,
+bit for bit."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1710_08471_gb300 as m
+
+    return m
+
+
+def check(A, Q, R, kappa, scale=1.0):
+    Qo, Ro = oracle.cqr2(A)
+    k = kappa or 2.0
+    assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
+    assert oracle.orthogonality(Q) <= scale * max(1e-12, 10 * oracle.orthogonality(Qo))
+    assert oracle.residual(A, Q, R) <= scale * max(1e-13, 10 * oracle.residual(A, Qo, Ro))
+    assert oracle.rel_error(R, Ro) <= scale * 1e-12 * k
+
+
+@pytest.mark.parametrize("prec,scale", [(0, 1.0), (1, 10.0)])
+def test_factor_rows_uneven_m(cq, prec, scale):
+    n = 64
+    with cq.Plan(6000, n, precision=prec) as p:
+        for m, kappa in [(6000, 1e4), (64, 10.0), (777, 1e3), (3001, None), (6000, 1e2)]:
+            A = synth.make_matrix(m, n, kappa, seed=m)
+            Q, R, info = p.factor_rows(to_dev(A))
+            assert info.status == 0
+            check(A, to_host(Q), to_host(R), kappa, scale)
+
+
+def test_lstsq_rows(cq):
+    n = 32
+    with cq.Plan(5000, n) as p:
+        for m in (5000, 100, 2047):
+            A = synth.make_matrix(m, n, 1e3, seed=m + 1)
+            b = synth.make_rhs(m, seed=m)
+            x, info = p.lstsq_rows(to_dev(A), to_dev(b))
+            xo = oracle.lstsq(A, b)
+            assert np.linalg.norm(to_host(x) - xo) <= 1e-12 * 1e3 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_matches_direct(cq, prec):
+    import torch
+
+    m, n = 8000, 96
+    A1 = to_dev(synth.make_matrix(m, n, 1e5, seed=1))
+    A2 = to_dev(synth.make_matrix(m, n, 1e3, seed=2))
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with cq.Plan(m, n, precision=prec) as p:
+        Qd, Rd, _ = p.factor(A1)
+        Qd2, Rd2, _ = p.factor(A2)
+    with cq.Plan(m, n, precision=prec, stream=s, graph=True) as p:
+        Q = cq.empty_colmajor(m, n, device="cuda")
+        R = cq.empty_colmajor(n, n, device="cuda")
+        for _ in range(3):  # capture, then replay twice
+            p.factor(A1, Q, R)
+            torch.cuda.synchronize()
+            assert bool((Q == Qd).all()) and bool((R == Rd).all())
+        p.factor(A2, Q, R)  # new arguments: a new capture
+        torch.cuda.synchronize()
+        assert bool((Q == Qd2).all()) and bool((R == Rd2).all())
+
+
+def _problems(cq, shapes, seed0=0):
+    mats, probs = [], []
+    for i, (m, n, kappa) in enumerate(shapes):
+        A = synth.make_matrix(m, n, kappa, seed=seed0 + i)
+        mats.append(A)
+        probs.append((to_dev(A), cq.empty_colmajor(m, n, device="cuda"), cq.empty_colmajor(n, n, device="cuda")))
+    return mats, probs
+
+
+SMALL = [(64, 1, None), (100, 8, 10.0), (4096, 64, None), (777, 33, 1e3), (2000, 64, 1e5), (65, 64, 1e2),
+         (31, 17, None), (5000, 48, 1e4)]
+MIXED = SMALL + [(20000, 128, 1e6), (3001, 200, 1e3), (30000, 64, 1e4), (1500, 300, 1e2)]
+
+
+def test_batch_grouped_kernel(cq):
+    mats, probs = _problems(cq, SMALL * 4, seed0=10)
+    with cq.Batch(len(probs), small_work_limit=1 << 40) as b:
+        infos = b.factor(probs)
+    for A, (_, Q, R), inf, (m, n, kappa) in zip(mats, probs, infos, SMALL * 4):
+        assert inf.status == 0
+        check(A, to_host(Q), to_host(R), kappa)
+
+
+@pytest.mark.parametrize("prec,scale", [(0, 1.0), (1, 10.0)])
+def test_batch_mixed_routing(cq, prec, scale):
+    mats, probs = _problems(cq, MIXED, seed0=50)
+    with cq.Batch(len(probs), precision=prec) as b:
+        infos = b.factor(probs)
+    for A, (_, Q, R), inf, (m, n, kappa) in zip(mats, probs, infos, MIXED):
+        assert inf.status == 0
+        # small problems run in the FP64 grouped kernel whatever the precision
+        check(A, to_host(Q), to_host(R), kappa, scale)
+
+
+def test_batch_breakdown_is_per_problem(cq):
+    shapes = [(500, 16, None), (600, 16, None), (700, 128, None), (800, 128, None)]
+    mats, probs = _problems(cq, shapes, seed0=90)
+    bad = [1, 3]
+    for i in bad:
+        mats[i][:, 5] = 0.0
+        probs[i][0].copy_(to_dev(mats[i]))
+    with cq.Batch(len(probs)) as b:
+        infos = b.factor(probs)
+    for i, inf in enumerate(infos):
+        if i in bad:
+            assert inf.status == cq.CQR2_ERR_NOT_SPD and inf.failed_pass == 1 and inf.failed_pivot == 5
+        else:
+            assert inf.status == 0
+            check(mats[i], to_host(probs[i][1]), to_host(probs[i][2]), None)
+
+
+def test_batch_result_same_alone_and_in_mix(cq):
+    """A problem's result does not depend on what else is in its batch."""
+    mats, probs = _problems(cq, MIXED, seed0=200)
+    with cq.Batch(len(probs)) as b:
+        b.factor(probs)
+        mixed = [(to_host(Q), to_host(R)) for _, Q, R in probs]
+        for i, pr in enumerate(probs):
+            b.factor([pr])
+            Q, R = to_host(pr[1]), to_host(pr[2])
+            assert np.array_equal(Q, mixed[i][0]) and np.array_equal(R, mixed[i][1]), i
+
+
+def test_autotune_records_table(cq):
+    res = cq.cqr2_autotune(50000, 128)
+    assert res["candidates"] >= 4 and res["gram_ctas"] in (1, 2, 4, 8) and res["ms"] > 0
+    table = cq.cqr2_tune_table()
+    assert "128:15:0" in table and "small_work_limit=" in table
+    # plans accept the tuned knobs
+    with cq.Plan(50000, 128, fused=True) as p:
+        p.set_gram_ctas(res["gram_ctas"])
+        p.set_fused(res["fused"])
+        A = synth.make_matrix(50000, 128, 1e4, seed=3)
+        Q, R, _ = p.factor(to_dev(A))
+    check(A, to_host(Q), to_host(R), 1e4)
