@@ -43,6 +43,8 @@ WORKLOADS = {
     "small": (4096, 64, None, 0, "FP64 CholeskyQR2, m=4096 n=64, iid N(0,1), kappa~1.3"),
     "square": (65536, 8192, 1e4, 2, "FP64 CholeskyQR2, m=65536 n=8192 (4.3 GB), kappa=1e4"),
     "wide512": (1 << 21, 512, 1e6, 3, "FP64 CholeskyQR2, m=2^21 n=512 (8.6 GB), kappa=1e6"),
+    # profiling size: larger than L2, a few GB on the device
+    "mid": (1 << 20, 128, 1e6, 1, "FP64 CholeskyQR2, m=2^20 n=128 (1.07 GB), kappa=1e6"),
 }
 
 # GB300 FP64: 2 DFMA per clock per SM (one warp instruction every 16 clocks
@@ -408,6 +410,24 @@ def bench_ours(args, ws, rank, local):
                       "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8,
                       "api": "cqr2_factor_host (pinned host buffers)"}
     plan.close()
+    if rank == 0 and not args.quick and args.serving_requests > 0:
+        # serving leg: a bounded stream of least-squares requests (Poisson
+        # arrivals at 2000/s, m in [1024, 262144], n in {16..256}, kappa in
+        # [1, 1e5]) under a 64 GB HBM budget, continuous batching over 8
+        # stream slots vs one request at a time
+        del A, Q, R
+        torch.cuda.empty_cache()
+        from paper_1710_08471_gb300 import serving
+
+        pool = serving.InputPool(262144, (16, 32, 64, 128, 256), seed=100)
+        sv = {}
+        for name, prec, slots in (("ozaki_continuous", 1, 8), ("ozaki_one_at_a_time", 1, 1),
+                                  ("fp64_continuous", 0, 8), ("fp64_one_at_a_time", 0, 1)):
+            try:
+                sv[name] = serving.run_workload(args.serving_requests, 2000.0, 100, prec, slots, 64e9, pool=pool)
+            except Exception as ex:  # a serving leg must not cost the main line
+                sv[name] = {"error": repr(ex)}
+        out["serving"] = sv
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -426,6 +446,8 @@ def main():
                     help="rows of the workload the CPU oracle runs on (default: all for the error check, "
                          "2^21 for --impl reference)")
     ap.add_argument("--quick", action="store_true", help="device timing only (no e2e / oracle legs)")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="requests in the serving leg (0 = skip)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

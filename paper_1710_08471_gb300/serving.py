@@ -174,6 +174,50 @@ def percentile(sorted_vals, q: float) -> float:
     return sorted_vals[f] + (sorted_vals[c] - sorted_vals[f]) * (k - f)
 
 
+def run_workload(count: int, rate: float, seed: int = 100, precision: int = cq.CQR2_FP64, slots: int = 8,
+                 budget: float = 64e9, m_max: int = 262144, n_values=(16, 32, 64, 128, 256),
+                 realtime: bool = True, pool: "InputPool | None" = None) -> dict:
+    """Serve a seeded least-squares request stream (synth.request_stream:
+    Poisson arrivals at `rate`, m uniform in [1024, m_max], n uniform over
+    n_values, kappa log-uniform in [1, 1e5]) and return latency/throughput."""
+    import synth
+
+    stream = synth.request_stream(count, seed=seed, rate=rate, m_lo=1024, m_hi=m_max, n_choices=tuple(n_values))
+    pool = pool or InputPool(m_max, n_values, seed=seed)
+    reqs = [pool.request(r["id"], r["t"], r["m"], r["n"], r["kappa"]) for r in stream]
+    srv = Server(budget, slots=slots, precision=precision, m_max=m_max, n_values=n_values)
+    try:
+        stats = srv.run(reqs, realtime=realtime)
+    finally:
+        srv.close()
+    done = [r for r in reqs if r.status == 0]
+    flops = sum(4.0 * r.m * r.n * r.n + 5.0 * r.n ** 3 / 3.0 + 2.0 * r.m * r.n for r in done)
+    stats["tflops"] = flops / stats["seconds"] / 1e12 if stats["seconds"] > 0 else float("nan")
+    stats.update({"requests": count, "rate_per_s": rate, "slots": slots, "precision": precision,
+                  "budget_gb": budget / 1e9, "m_max": m_max, "n_values": list(n_values)})
+    return stats
+
+
+def main(argv=None) -> None:
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="least-squares serving benchmark over CholeskyQR2")
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--precision", type=int, default=cq.CQR2_OZAKI_BF16)
+    ap.add_argument("--seed", type=int, default=100)
+    args = ap.parse_args(argv)
+    pool = InputPool(262144, (16, 32, 64, 128, 256), seed=args.seed)
+    out = {"continuous": run_workload(args.requests, args.rate, args.seed, args.precision, args.slots,
+                                      args.budget_gb * 1e9, pool=pool),
+           "one_at_a_time": run_workload(args.requests, args.rate, args.seed, args.precision, 1,
+                                         args.budget_gb * 1e9, pool=pool)}
+    print(json.dumps(out))
+
+
 class InputPool:
     """Device-resident synthetic inputs for request streams: for every n and
     a few condition-number buckets, one m_max x n matrix built by the seeded
@@ -203,3 +247,7 @@ class InputPool:
     def request(self, rid: int, t: float, m: int, n: int, kappa: float) -> Request:
         i = self.bucket(kappa)
         return Request(id=rid, t_arrival=t, m=m, n=n, A_src=self.A[(n, i)][:m], b_src=self.b[:m])
+
+
+if __name__ == "__main__":
+    main()
