@@ -16,6 +16,9 @@ from .cholqr2 import (  # noqa: F401
     q_rows,
     rel_error,
     residual,
+    scqr3,
+    shift_of,
+    shifted_cqr,
     syrk,
 )
 from .householder import householder_qr  # noqa: F401

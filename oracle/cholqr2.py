@@ -158,6 +158,53 @@ def cqr2(A: np.ndarray, keep: bool = False):
     return Q, R, info
 
 
+UNIT_ROUNDOFF = 2.0 ** -53
+
+
+def shift_of(W: np.ndarray, m: int) -> float:
+    """Shift of the shifted CholeskyQR pass: s = 11 (m n + n (n+1)) u ||A||_F^2
+    with ||A||_F^2 = trace(W) (the published choice for the unconditionally
+    stable variant the paper cites in Section I and names as future work in
+    Section V; ||A||_2^2 <= ||A||_F^2 keeps it a safe upper bound)."""
+    n = W.shape[0]
+    return 11.0 * (m * n + n * (n + 1)) * UNIT_ROUNDOFF * float(np.trace(W))
+
+
+def shifted_cqr(A: np.ndarray) -> tuple[np.ndarray, np.ndarray, dict]:
+    """One shifted CholeskyQR pass: W = A^T A + s I, [L, Y] = CholInv(W),
+    R = L^T, Q = A R^-1. Q is not orthonormal but well conditioned, which is
+    what the following CholeskyQR2 needs."""
+    A = np.asarray(A, dtype=np.float64)
+    W = syrk(A)
+    s = shift_of(W, A.shape[0])
+    Ws = W + s * np.eye(W.shape[0])
+    L, Y = cholinv(Ws)
+    R = np.ascontiguousarray(L.T)
+    Q = A @ np.ascontiguousarray(Y.T)
+    return Q, R, dict(W=W, shift=s)
+
+
+def scqr3(A: np.ndarray, keep: bool = False):
+    """Shifted CholeskyQR3: (Q0, R0) = shifted CQR(A); (Q, R') = CQR2(Q0);
+    R = R' R0."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if m < n or n < 1:
+        raise ValueError("sCQR3 needs an m x n matrix with m >= n >= 1")
+    try:
+        Q0, R0, i0 = shifted_cqr(A)
+    except NotSPD as e:
+        raise PassFailed(1, e) from None
+    try:
+        Q, Rp = cqr2(Q0)
+    except PassFailed as e:
+        raise PassFailed(e.pass_no + 1, e) from None
+    R = np.triu(Rp @ R0)
+    if keep:
+        return Q, R, dict(Q0=Q0, R0=R0, Rp=Rp, **i0)
+    return Q, R
+
+
 def back_substitution(R: np.ndarray, c: np.ndarray) -> np.ndarray:
     """Solve R x = c for upper-triangular R, last unknown first."""
     n = R.shape[0]

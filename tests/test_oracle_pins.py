@@ -286,3 +286,45 @@ def test_pins_accept_oracle():
 @pytest.mark.parametrize("key", sorted(_MUTATIONS))
 def test_pins_reject_planted_mistake(key):
     assert not _pins_pass(_mutant(key))
+
+
+# ------------------------------------------- shifted CholeskyQR3 (NEXT row)
+
+def test_shift_formula():
+    A = synth.make_matrix(300, 12, 1e3, seed=41)
+    W = oracle.syrk(A)
+    s = oracle.shift_of(W, 300)
+    assert s == pytest.approx(11 * (300 * 12 + 12 * 13) * EPS * np.linalg.norm(A) ** 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e9, 1e12])
+def test_scqr3_unconditionally_stable(kappa):
+    m, n = 4096, 48
+    A = synth.make_matrix(m, n, kappa, seed=42)
+    Q, R = oracle.scqr3(A)
+    assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
+    assert oracle.orthogonality(Q) <= 100 * n * EPS
+    assert oracle.residual(A, Q, R) <= 100 * n * EPS
+    Qh, Rh = oracle.householder_qr(A)
+    # both are backward stable: R agrees with Householder's far better than kappa eps
+    assert oracle.rel_error(R, Rh) <= 1e-12
+
+
+def test_scqr3_where_cqr2_breaks_down():
+    A = synth.make_matrix(2048, 32, 1e10, seed=43)
+    with pytest.raises(oracle.NotSPD):
+        oracle.cqr2(A)
+    Q, R = oracle.scqr3(A)
+    assert oracle.orthogonality(Q) <= 100 * 32 * EPS
+
+
+def test_scqr3_needs_the_shift():
+    # planted mistake: without the shift the first pass breaks down at kappa 1e10
+    A = synth.make_matrix(2048, 32, 1e10, seed=43)
+    src = inspect.getsource(ocq)
+    old = "    Ws = W + s * np.eye(W.shape[0])"
+    assert src.count(old) == 1
+    mod = types.ModuleType("oracle_mutant_noshift")
+    exec(compile(src.replace(old, "    Ws = W"), "<mutant noshift>", "exec"), mod.__dict__)
+    with pytest.raises(mod.NotSPD):
+        mod.scqr3(A)
