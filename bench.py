@@ -157,14 +157,24 @@ def dist_env():
 
 
 def allreduce_max(x: float, ws: int) -> float:
+    """Largest value over the ranks (host-side timing aggregation only; the
+    factorizations themselves exchange nothing)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(ws: int, flops_per_replica: float, ms_local: float) -> tuple[float, float]:
+    """Whole-job TFLOP/s of ws independent replicas timed by the slowest rank:
+    (value, ms_per_step)."""
+    ms = allreduce_max(ms_local, ws)
+    return ws * flops_per_replica / (ms * 1e-3) / 1e12, ms
 
 
 def barrier(ws: int):
@@ -334,9 +344,8 @@ def bench_ours(args, ws, rank, local):
     clocks.start()
     ms_local, launches, per_stage = timed(plan, args.steps, args.warmup, True)
     clk = clocks.stop()
-    ms_step = allreduce_max(ms_local, ws)
     flops = nominal_flops(m, n)
-    value = ws * flops / (ms_step * 1e-3) / 1e12
+    value, ms_step = replica_throughput(ws, flops, ms_local)
     fp64_peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
 
     out = {
@@ -406,8 +415,17 @@ def bench_ours(args, ws, rank, local):
             plan.factor_host(hA, hQ, hR)
             times.append(time.perf_counter() - t0)
         e2e_ms = 1e3 * statistics.median(times)
+        # one more call with the stage timers on, for the copy bandwidths
+        plan.set_profiling(True)
+        plan.factor_host(hA, hQ, hR)
+        st_e = plan.stage_times()
+        plan.set_profiling(False)
+        h2d_ms, d2h_ms = st_e["h2d"][0], st_e["d2h"][0]
         out["e2e"] = {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                       "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": m * n * 8 + n * n * 8,
+                      "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
+                      "h2d_gbs": m * n * 8 / (h2d_ms * 1e-3) / 1e9 if h2d_ms else None,
+                      "d2h_gbs": (m * n * 8 + n * n * 8) / (d2h_ms * 1e-3) / 1e9 if d2h_ms else None,
                       "api": "cqr2_factor_host (pinned host buffers)"}
     plan.close()
     if rank == 0 and not args.quick and args.serving_requests > 0:

@@ -69,6 +69,15 @@ typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2
                            produced and its Gram accumulated in one sweep, so
                            Q1 makes one fewer trip through memory (FP64,
                            n <= 128; ignored otherwise) */
+#define CQR2_SHIFTED 0x4u /* shifted CholeskyQR3: a first CholeskyQR pass on
+                             A^T A + s I with s = 11 (m n + n (n+1)) 2^-53
+                             ||A||_F^2, then CholeskyQR2 of its Q; R is the
+                             product of the three R factors. The third-pass,
+                             shifted variant the paper cites for unconditional
+                             stability (Section I) and names as future work
+                             (Section V): accurate to kappa(A) near 1e12, where
+                             plain CholeskyQR2 breaks down. Breakdown passes
+                             are reported as 1 (shifted), 2 and 3. */
 #define CQR2_GRAPH 0x2u /* capture the launch sequence of a factorization in
                            a CUDA graph and replay it while the call's
                            pointers, leading dimensions and m repeat; needs a

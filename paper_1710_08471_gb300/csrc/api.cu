@@ -40,6 +40,8 @@ struct cqr2_plan_st {
   double* U = nullptr;
   double* R1 = nullptr;
   double* Rf = nullptr;  // final R when the caller passes no R
+  double* R0 = nullptr;  // R of the shifted pass (CQR2_SHIFTED)
+  double* Rt = nullptr;  // R of the CholeskyQR2 that follows it
   double* Rp = nullptr;
   double* Q1 = nullptr;  // m x n, only when !small
   double* lspart = nullptr;
@@ -158,11 +160,11 @@ cqr2_status_t set_rows(cqr2_plan_st* p, int64_t m) {
 // Split-precision CholeskyQR2: the Gram and Q-forming contractions on the
 // BF16 tensor cores (Ozaki slices), CholInv and R2 R1 in native FP64.
 cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
-                                int64_t ldr) {
+                                int64_t ldr, int pass_base = 0) {
   const int n = (int)p->n, S = p->oz_S;
   const int64_t m = p->cm;
   cudaStream_t s = p->stream;
-  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  if (!pass_base) TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   for (int pass = 1; pass <= 2; ++pass) {
     const double* X = pass == 1 ? dA : dQ;
     const int64_t ldx = pass == 1 ? lda : ldq;
@@ -177,7 +179,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
-      TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s));
+      TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + pass, s));
       if (pass == 1) TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
     }
     {
@@ -200,11 +202,11 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
 }
 
 cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
-                          int64_t ldr) {
-  if (p->oz_S) return factor_impl_ozaki(p, dA, lda, dQ, ldq, dR, ldr);
+                          int64_t ldr, int pass_base = 0) {
+  if (p->oz_S) return factor_impl_ozaki(p, dA, lda, dQ, ldq, dR, ldr, pass_base);
   const int n = (int)p->n;
   cudaStream_t s = p->stream;
-  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  if (!pass_base) TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   // ---- pass 1: W1 = A^T A, [L1, Y1] = CholInv(W1)
   {
     Stage st(p, CQR2_STAGE_GRAM1);
@@ -213,7 +215,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
-    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
+    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + 1, s));
     TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
   }
   // ---- Q1 = A R1^-1 (staged in dQ on the small path), then pass 2 on Q1
@@ -241,7 +243,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV2);
-    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 2, s));
+    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + 2, s));
   }
   {
     Stage st(p, CQR2_STAGE_QFORM2);
@@ -258,6 +260,54 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
     TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
                  GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
   }
+  return CQR2_OK;
+}
+
+// CholeskyQR2, or with CQR2_SHIFTED shifted CholeskyQR3: a shifted first
+// pass (W = A^T A + s I, [L0, Y0] = CholInv(W), Q0 = A Y0^T staged in Q),
+// CholeskyQR2 of Q0 in place (its passes report as 2 and 3), R = R' R0.
+cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                         int64_t ldr) {
+  if (!(p->flags & CQR2_SHIFTED)) return factor_impl(p, dA, lda, dQ, ldq, dR, ldr, 0);
+  const int n = (int)p->n;
+  const int64_t m = p->cm;
+  cudaStream_t s = p->stream;
+  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  {
+    Stage st(p, CQR2_STAGE_GRAM1);
+    if (p->oz_S) {
+      TRY(ozaki_colmax(dA, lda, m, n, p->oz_colmax, p->oz_cexp, s));
+      TRY(ozaki_slice_cols(dA, lda, m, n, p->oz_S, p->oz_cexp, p->oz_planes, s));
+      TRY(ozaki_gram(p->oz_maps, m, n, p->oz_S, p->oz_cexp, p->oz_partial, p->W, n, p->st, s));
+    } else {
+      TRY(gram_partials(dA, lda, m, n, p->g, p->partial, s));
+      TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+    }
+    TRY(add_shift(p->W, n, n, m, s));
+  }
+  {
+    Stage st(p, CQR2_STAGE_CHOLINV1);
+    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
+    TRY(transpose_lower(p->L, n, n, p->R0, n, s));  // R0 = L0^T
+  }
+  {
+    Stage st(p, CQR2_STAGE_QFORM1);
+    if (p->oz_S) {
+      TRY(ozaki_slice_rinv(p->Y, n, n, p->oz_S, false, p->oz_rinv, p->oz_fexp, s));
+      TRY(ozaki_slice_rows(dA, lda, m, n, p->oz_S, p->oz_planes, p->oz_rexp, s));
+      TRY(ozaki_qform(p->oz_maps, m, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, s));
+    } else if (p->small) {
+      TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
+      TRY(qform_small(dA, lda, m, n, p->Rp, dQ, ldq, s));
+    } else {
+      TRY(gemm_f64(m, n, n, 1.0, dA, lda, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    }
+  }
+  cqr2_status_t r = factor_impl(p, dQ, ldq, dQ, ldq, p->Rt, n, 1);
+  if (r != CQR2_OK) return r;
+  Stage st(p, CQR2_STAGE_TRMM);
+  TRY(gemm_f64(n, n, n, 1.0, p->Rt, n, p->R0, n, 0.0, dR, ldr,
+               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
   return CQR2_OK;
 }
 
@@ -291,7 +341,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (n < 1 || m < n || n > 65535) return CQR2_ERR_INVALID_ARG;
   if (precision != CQR2_FP64 && precision != CQR2_OZAKI_BF16 && precision != CQR2_OZAKI_BF16_S6)
     return CQR2_ERR_INVALID_ARG;
-  if (flags & ~(CQR2_FUSED | CQR2_GRAPH)) return CQR2_ERR_INVALID_ARG;
+  if (flags & ~(CQR2_FUSED | CQR2_GRAPH | CQR2_SHIFTED)) return CQR2_ERR_INVALID_ARG;
   const int oz_S = precision == CQR2_OZAKI_BF16 ? 7 : (precision == CQR2_OZAKI_BF16_S6 ? 6 : 0);
   if (oz_S && !ozaki_supported((int)n, oz_S)) return CQR2_ERR_UNSUPPORTED;
   int dev = 0;
@@ -335,14 +385,16 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   take((p->small || oz_S) ? 0 : (size_t)m * n * sizeof(double));    // 9 Q1
   take((size_t)p->gemv_nsplit * n * sizeof(double));                 // 10 lspart
   take(sizeof(DevStatus));                                           // 11 st
+  take(nn);                                                          // 12 R0
+  take(nn);                                                          // 13 Rt
   if (oz_S) {
-    take(ozaki_plane_elems(m, (int)n, oz_S) * 2);                    // 12 slice planes (bf16)
-    take((size_t)oz_S * n * og.np * 2);                              // 13 R^-1 planes
-    take((size_t)n * sizeof(unsigned long long));                    // 14 column max
-    take((size_t)n * sizeof(int));                                   // 15 column exponents
-    take((size_t)m * sizeof(int));                                   // 16 row exponents
-    take((size_t)n * sizeof(int));                                   // 17 R^-1 exponents
-    take((size_t)og.nsplit * n * n * sizeof(double));                // 18 Gram partials
+    take(ozaki_plane_elems(m, (int)n, oz_S) * 2);                    // 14 slice planes (bf16)
+    take((size_t)oz_S * n * og.np * 2);                              // 15 R^-1 planes
+    take((size_t)n * sizeof(unsigned long long));                    // 16 column max
+    take((size_t)n * sizeof(int));                                   // 17 column exponents
+    take((size_t)m * sizeof(int));                                   // 18 row exponents
+    take((size_t)n * sizeof(int));                                   // 19 R^-1 exponents
+    take((size_t)og.nsplit * n * n * sizeof(double));                // 20 Gram partials
   }
   if (cudaMalloc(&p->ws, sz) != cudaSuccess) {
     cudaGetLastError();
@@ -365,18 +417,20 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->U = at(5);
   p->R1 = at(6);
   p->Rf = at(7);
+  p->R0 = at(12);
+  p->Rt = at(13);
   p->Rp = at(8);
   p->Q1 = p->small ? nullptr : at(9);
   p->lspart = at(10);
   p->st = reinterpret_cast<DevStatus*>(p->ws + off[11]);
   if (oz_S) {
-    p->oz_planes = reinterpret_cast<unsigned short*>(p->ws + off[12]);
-    p->oz_rinv = reinterpret_cast<unsigned short*>(p->ws + off[13]);
-    p->oz_colmax = reinterpret_cast<unsigned long long*>(p->ws + off[14]);
-    p->oz_cexp = reinterpret_cast<int*>(p->ws + off[15]);
-    p->oz_rexp = reinterpret_cast<int*>(p->ws + off[16]);
-    p->oz_fexp = reinterpret_cast<int*>(p->ws + off[17]);
-    p->oz_partial = at(18);
+    p->oz_planes = reinterpret_cast<unsigned short*>(p->ws + off[14]);
+    p->oz_rinv = reinterpret_cast<unsigned short*>(p->ws + off[15]);
+    p->oz_colmax = reinterpret_cast<unsigned long long*>(p->ws + off[16]);
+    p->oz_cexp = reinterpret_cast<int*>(p->ws + off[17]);
+    p->oz_rexp = reinterpret_cast<int*>(p->ws + off[18]);
+    p->oz_fexp = reinterpret_cast<int*>(p->ws + off[19]);
+    p->oz_partial = at(20);
     // zero the planes once so that padding rows/columns read as zero
     if (cudaMemsetAsync(p->oz_planes, 0, ozaki_plane_elems(m, (int)n, oz_S) * 2, p->stream) != cudaSuccess ||
         cudaMemsetAsync(p->oz_rinv, 0, (size_t)oz_S * n * og.np * 2, p->stream) != cudaSuccess ||
@@ -448,7 +502,7 @@ cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64
       p->gexec = nullptr;
       p->graph = nullptr;
       TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-      r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr);
+      r = factor_any(p, dA, lda, dQ, ldq, dR, ldr);
       cudaGraph_t g = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
       if (r != CQR2_OK || ce != cudaSuccess) {
@@ -470,7 +524,7 @@ cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64
       p->gkey.m = m;
     }
     TRY(cudaGraphLaunch(p->gexec, p->stream));
-  } else if ((r = factor_impl(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) {
+  } else if ((r = factor_any(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) {
     return r;
   }
   if (info) return read_info(p, info);
@@ -522,7 +576,7 @@ cqr2_status_t cqr2_lstsq_rows(cqr2_plan_t p, int64_t m, const double* dA, int64_
   if ((r = set_rows(p, m)) != CQR2_OK) return r;
   double* R = dR ? dR : p->Rf;
   const int64_t ldR = dR ? ldr : p->n;
-  if ((r = factor_impl(p, dA, lda, dQ, ldq, R, ldR)) != CQR2_OK) return r;
+  if ((r = factor_any(p, dA, lda, dQ, ldq, R, ldR)) != CQR2_OK) return r;
   {
     Stage st(p, CQR2_STAGE_LSTSQ);
     TRY(gemv_t_partials(dQ, ldq, p->cm, (int)p->n, db, p->gemv_nsplit, p->lspart, p->stream));
@@ -655,7 +709,7 @@ cqr2_status_t cqr2_factor_host(cqr2_plan_t p, const double* hA, int64_t lda, dou
     TRY(cudaMemcpy2DAsync(p->hA_dev, rowb, hA, (size_t)lda * sizeof(double), rowb, (size_t)p->n,
                           cudaMemcpyHostToDevice, p->stream));
   }
-  if ((r = factor_impl(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n)) != CQR2_OK) return r;
+  if ((r = factor_any(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n)) != CQR2_OK) return r;
   {
     Stage st(p, CQR2_STAGE_D2H);
     TRY(cudaMemcpy2DAsync(hQ, (size_t)ldq * sizeof(double), p->hQ_dev, rowb, rowb, (size_t)p->n,

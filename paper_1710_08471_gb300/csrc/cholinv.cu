@@ -145,6 +145,29 @@ cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl,
   return rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s);
 }
 
+// Shift of the shifted CholeskyQR pass: W += s I with
+// s = 11 (m n + n (n+1)) u trace(W), u = 2^-53 (||A||_F^2 = trace(A^T A)).
+// One CTA; the trace is summed in a fixed order.
+__global__ void __launch_bounds__(256) k_add_shift(double* __restrict__ W, int64_t ldw, int n, int64_t m) {
+  __shared__ double part[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) t += W[i + (int64_t)i * ldw];
+  part[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double s = 11.0 * ((double)m * n + (double)n * (n + 1)) * 0x1p-53 * part[0];
+  for (int i = threadIdx.x; i < n; i += 256) W[i + (int64_t)i * ldw] += s;
+}
+
+cudaError_t add_shift(double* W, int64_t ldw, int n, int64_t m, cudaStream_t s) {
+  k_add_shift<<<1, 256, 0, s>>>(W, ldw, n, m);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int64_t ldr, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32));
   k_transpose_lower<<<grid, dim3(32, 8), 0, s>>>(L, ldl, n, R, ldr);

@@ -76,6 +76,8 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
 constexpr int CHOLINV_BASE = 64;
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                     double* work, double* U, DevStatus* st, int pass, cudaStream_t s);
+// Shifted CholeskyQR: W += s I, s = 11 (m n + n (n+1)) 2^-53 trace(W).
+cudaError_t add_shift(double* W, int64_t ldw, int n, int64_t m, cudaStream_t s);
 // R = L^T (upper) with zeros below the diagonal.
 cudaError_t transpose_lower(const double* L, int64_t ldl, int n, double* R, int64_t ldr, cudaStream_t s);
 // R = upper part of X with zeros below the diagonal.

@@ -470,17 +470,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(const __grid_const
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint64_t da = sdesc(sA + slot * A_BYTES);
-          for (int t = 0; t + s < S; ++t) {
-            const int g = s + t;
+          // Products (s, t) for t = t0 .. t0+nt-1 in one MMA of N = 64 nt: the
+          // B slices lie back to back in shared memory (one 1024-byte group
+          // pitch throughout) and the groups g = s + t are adjacent 64-column
+          // accumulators in TMEM, so the wide MMA lands every product in its
+          // own group.
+          for (int t0 = 0; t0 + s < S && ok; t0 += 4) {
+            const int nt = min(4, S - s - t0);
             if (first && s == 0 && c >= 1) {
-              ok = mbar_wait(&accempty[g], (c - 1) & 1, p.st);
+              for (int g = t0; g < t0 + nt && ok; ++g) ok = mbar_wait(&accempty[g], (c - 1) & 1, p.st);
               if (!ok) break;
               asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            const uint64_t db = sdesc(sB + (buf * S + t) * B_BYTES);
+            const uint32_t idesc_n = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((OZ_BN * nt) >> 3) << 17);
+            const uint64_t db = sdesc(sB + (buf * S + t0) * B_BYTES);
 #pragma unroll
             for (int k = 0; k < OZ_BK / 16; ++k)
-              mma_bf16(tmem + (uint32_t)(g * OZ_BN), da + 2 * k, db + 2 * k, idesc,
+              mma_bf16(tmem + (uint32_t)((s + t0) * OZ_BN), da + 2 * k, db + 2 * k, idesc_n,
                        (first && s == 0 && k == 0) ? 0u : 1u);
           }
           mma_commit(&aempty[slot]);

@@ -49,24 +49,27 @@ class Request:
         return 8 * (2 * self.m * self.n + self.n * self.n + self.m + self.n)
 
 
-class Server:
-    def __init__(self, budget_bytes: float, slots: int = 8, precision: int = cq.CQR2_FP64, m_max: int = 262144,
-                 n_values=(16, 32, 64, 128, 256), keep_outputs: bool = False):
+class CudaExecutor:
+    """Runs requests on CUDA stream slots through cqr2_lstsq_rows, one plan
+    per (slot, n) sized for the largest m."""
+
+    def __init__(self, slots: int, precision: int, m_max: int, n_values, keep_outputs: bool = False):
         import torch
 
         self.torch = torch
-        self.budget = float(budget_bytes)
         self.precision = precision
         self.m_max = int(m_max)
         self.keep = keep_outputs
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.plans = [dict() for _ in range(slots)]
-        self.busy = [None] * slots  # (request, event)
-        self.inflight_bytes = 0
         self.workspace_bytes = 0
         for s in range(slots):
             for n in n_values:
                 self._plan(s, n)
+
+    @property
+    def slots(self) -> int:
+        return len(self.streams)
 
     def _plan(self, slot: int, n: int):
         p = self.plans[slot].get(n)
@@ -77,7 +80,12 @@ class Server:
             self.workspace_bytes += p.workspace_bytes
         return p
 
-    def _submit(self, r: Request, slot: int, t0: float):
+    def sync(self) -> None:
+        self.torch.cuda.synchronize()
+
+    def submit(self, r: Request, slot: int):
+        """Enqueue the copy-in and the solve on the slot's stream; returns a
+        handle that keeps the request's buffers alive."""
         torch = self.torch
         s = self.streams[slot]
         with torch.cuda.stream(s):
@@ -91,49 +99,90 @@ class Server:
             cq.cqr2_lstsq_rows(plan.handle, r.m, r.n, A, b, x, Q, R, sync=False)
             ev = torch.cuda.Event()
             ev.record(s)
-        r.t_admit = time.perf_counter() - t0
-        r.slot = slot
-        # hold the buffers until completion
-        self.busy[slot] = (r, ev, (A, b, Q, R, x), plan)
-        self.inflight_bytes += r.bytes
+        return (ev, (A, b, Q, R, x), plan)
 
-    def _retire(self, slot: int, t0: float):
-        r, ev, bufs, plan = self.busy[slot]
-        r.t_done = time.perf_counter() - t0
+    def poll(self, handle) -> bool:
+        return handle[0].query()
+
+    def finish(self, r: Request, handle) -> None:
+        ev, (A, b, Q, R, x), plan = handle
         info = N.Info()
         # status word of the plan's last call: the slot's stream has finished it
         N.load().cqr2_plan_info(plan.handle, info)
         r.status = info.status
-        A, b, Q, R, x = bufs
         r.x = x
         if self.keep:
             r.Q, r.R = Q, R
+
+    def close(self) -> None:
+        for d in self.plans:
+            for p in d.values():
+                p.close()
+        self.plans = []
+
+
+class Server:
+    """Continuous-batching scheduler: FIFO queue, admission against an HBM
+    budget into free slots, completion by polling. The executor runs the
+    requests (CudaExecutor by default); clock and sleep can be replaced for
+    deterministic tests."""
+
+    def __init__(self, budget_bytes: float, slots: int = 8, precision: int = cq.CQR2_FP64, m_max: int = 262144,
+                 n_values=(16, 32, 64, 128, 256), keep_outputs: bool = False, executor=None, clock=None,
+                 sleep=None):
+        self.exec = executor if executor is not None else CudaExecutor(slots, precision, m_max, n_values,
+                                                                       keep_outputs)
+        self.clock = clock or time.perf_counter
+        self.sleep = sleep or time.sleep
+        self.budget = float(budget_bytes)
+        self.busy = [None] * self.exec.slots  # (request, handle)
+        self.inflight_bytes = 0
+        self.peak_inflight_bytes = 0
+        self.admitted: list[int] = []
+
+    @property
+    def workspace_bytes(self) -> int:
+        return self.exec.workspace_bytes
+
+    def _submit(self, r: Request, slot: int, t0: float):
+        handle = self.exec.submit(r, slot)
+        r.t_admit = self.clock() - t0
+        r.slot = slot
+        self.busy[slot] = (r, handle)
+        self.inflight_bytes += r.bytes
+        self.peak_inflight_bytes = max(self.peak_inflight_bytes, self.inflight_bytes)
+        self.admitted.append(r.id)
+
+    def _retire(self, slot: int, t0: float):
+        r, handle = self.busy[slot]
+        r.t_done = self.clock() - t0
+        self.exec.finish(r, handle)
         self.busy[slot] = None
         self.inflight_bytes -= r.bytes
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
-        """Serve `requests` (sorted by arrival). With realtime, a request is
-        not admitted before its arrival time; otherwise all are available at 0."""
+        """Serve `requests`. With realtime, a request is not admitted before
+        its arrival time; otherwise all are available at time 0."""
         queue = collections.deque()
         pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
         done = []
-        self.torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        slots = len(self.streams)
+        self.exec.sync()
+        t0 = self.clock()
+        slots = len(self.busy)
         limit = self.budget - self.workspace_bytes
         while pending or queue or any(b is not None for b in self.busy):
-            now = time.perf_counter() - t0
+            now = self.clock() - t0
             while pending and (not realtime or pending[0].t_arrival <= now):
                 queue.append(pending.popleft())
             for s in range(slots):
-                if self.busy[s] is not None and self.busy[s][1].query():
+                if self.busy[s] is not None and self.exec.poll(self.busy[s][1]):
                     done.append(self.busy[s][0])
                     self._retire(s, t0)
             while queue and queue[0].bytes > limit:
                 # larger than the whole budget: it can never be admitted
                 r = queue.popleft()
                 r.status = N.CQR2_ERR_OOM
-                r.t_done = time.perf_counter() - t0
+                r.t_done = self.clock() - t0
                 done.append(r)
             for s in range(slots):
                 if not queue:
@@ -142,10 +191,10 @@ class Server:
                     self._submit(queue.popleft(), s, t0)
             if not queue and pending and realtime:
                 # idle until the next arrival
-                wait = pending[0].t_arrival - (time.perf_counter() - t0)
+                wait = pending[0].t_arrival - (self.clock() - t0)
                 if wait > 0 and all(b is None for b in self.busy):
-                    time.sleep(min(wait, 0.001))
-        t_end = time.perf_counter() - t0
+                    self.sleep(min(wait, 0.001))
+        t_end = self.clock() - t0
         lat = sorted((r.t_done - r.t_arrival) for r in done) if realtime else sorted(r.t_done for r in done)
         return {
             "completed": len(done),
@@ -156,13 +205,11 @@ class Server:
             "p99_ms": 1e3 * percentile(lat, 99),
             "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
             "workspace_bytes": self.workspace_bytes,
+            "peak_inflight_gb": self.peak_inflight_bytes / 1e9,
         }
 
     def close(self):
-        for d in self.plans:
-            for p in d.values():
-                p.close()
-        self.plans = []
+        self.exec.close()
 
 
 def percentile(sorted_vals, q: float) -> float:
