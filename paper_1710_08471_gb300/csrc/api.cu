@@ -21,6 +21,8 @@ struct cqr2_plan_st {
   int64_t m = 0, n = 0;  // m is the largest row count the plan serves
   int64_t cm = 0;        // row count of the call in progress (geometry below is for cm)
   int gram_cps = 4;      // Gram CTAs per SM (autotuned knob, 1..GRAM_CPS_MAX)
+  int64_t gram_cap = 0;  // row ranges the Gram partials have room for (any cm <= m)
+  int64_t oz_cap = 0;    // same for the split-precision Gram partials
   int precision = CQR2_FP64;
   unsigned flags = 0;
   int device = 0;
@@ -87,6 +89,16 @@ constexpr int GRAM_CPS_MAX = 8;
     if (e_ != cudaSuccess) return CQR2_ERR_CUDA; \
   } while (0)
 
+// Copy a column-major rows x cols block: one linear copy when both sides are
+// packed (ld == rows), which runs at full link bandwidth, else a pitched copy.
+cudaError_t copy_cols(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+  const size_t colb = (size_t)rows * sizeof(double);
+  if (ldd == rows && lds == rows) return cudaMemcpyAsync(dst, src, colb * (size_t)cols, kind, s);
+  return cudaMemcpy2DAsync(dst, (size_t)ldd * sizeof(double), src, (size_t)lds * sizeof(double), colb, (size_t)cols,
+                           kind, s);
+}
+
 cqr2_status_t check_device(const cqr2_plan_st* p) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return CQR2_ERR_CUDA;
@@ -147,7 +159,7 @@ namespace {
 cqr2_status_t set_rows(cqr2_plan_st* p, int64_t m) {
   if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
   if (m == p->cm) return CQR2_OK;
-  p->g = gram_geometry(m, (int)p->n, 0, p->gram_cps);
+  p->g = gram_geometry(m, (int)p->n, p->gram_cap, p->gram_cps);
   p->gemv_nsplit = gemv_splits(m, (int)p->n);
   if (p->oz_S && ozaki_make_maps(p->oz_maps, m, (int)p->n, p->oz_S, p->oz_planes, p->oz_rinv) != cudaSuccess) {
     p->cm = 0;
@@ -175,7 +187,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_GRAM1 : CQR2_STAGE_GRAM2);
-      TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->W, n, p->st, s));
+      TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->oz_cap, p->W, n, p->st, s));
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
@@ -278,7 +290,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
     if (p->oz_S) {
       TRY(ozaki_colmax(dA, lda, m, n, p->oz_colmax, p->oz_cexp, s));
       TRY(ozaki_slice_cols(dA, lda, m, n, p->oz_S, p->oz_cexp, p->oz_planes, s));
-      TRY(ozaki_gram(p->oz_maps, m, n, p->oz_S, p->oz_cexp, p->oz_partial, p->W, n, p->st, s));
+      TRY(ozaki_gram(p->oz_maps, m, n, p->oz_S, p->oz_cexp, p->oz_partial, p->oz_cap, p->W, n, p->st, s));
     } else {
       TRY(gram_partials(dA, lda, m, n, p->g, p->partial, s));
       TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
@@ -354,7 +366,15 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->flags = flags;
   p->device = dev;
   p->stream = static_cast<cudaStream_t>(stream);
-  p->g = gram_geometry(m, (int)n, 0, GRAM_CPS_MAX);  // size the partials for the largest split
+  // Size the Gram partials for every row count the plan serves: a smaller m
+  // can round to more (shorter) ranges than m itself, up to the CTA target.
+  p->g = gram_geometry(m, (int)n, 0, GRAM_CPS_MAX);
+  {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    p->gram_cap = std::max<int64_t>(p->g.nsplit, ceil_div((int64_t)GRAM_CPS_MAX * sms, p->g.ntiles_total));
+    p->g.nsplit = p->gram_cap;
+  }
   p->small = qform_group_width((int)n) > 0;
   p->fused = (flags & CQR2_FUSED) && qform_gram_fusable((int)n);
   p->gemv_nsplit = gemv_splits(m, (int)n);
@@ -363,6 +383,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   OzGeom og;
   if (oz_S) {
     og = ozaki_geometry(m, (int)n);
+    p->oz_cap = ozaki_split_capacity(m, (int)n);
     p->small = false;  // no m x n FP64 workspace: Q1 is staged in the output Q
     p->fused = false;
   }
@@ -394,7 +415,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
     take((size_t)n * sizeof(int));                                   // 17 column exponents
     take((size_t)m * sizeof(int));                                   // 18 row exponents
     take((size_t)n * sizeof(int));                                   // 19 R^-1 exponents
-    take((size_t)og.nsplit * n * n * sizeof(double));                // 20 Gram partials
+    take((size_t)p->oz_cap * n * n * sizeof(double));                // 20 Gram partials
   }
   if (cudaMalloc(&p->ws, sz) != cudaSuccess) {
     cudaGetLastError();
@@ -442,7 +463,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
       return CQR2_ERR_CUDA;
     }
   }
-  p->g = gram_geometry(m, (int)n, 0, p->gram_cps);
+  p->g = gram_geometry(m, (int)n, p->gram_cap, p->gram_cps);
   p->cm = m;  // geometry and tensor maps above are for the full row count
   std::memset(p->h_st, 0, sizeof(DevStatus));
   if (cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream) != cudaSuccess) {
@@ -596,7 +617,7 @@ cqr2_status_t cqr2_syrk(cqr2_plan_t p, const double* dA, int64_t lda, double* dW
     TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
     TRY(ozaki_colmax(dA, lda, p->cm, n, p->oz_colmax, p->oz_cexp, p->stream));
     TRY(ozaki_slice_cols(dA, lda, p->cm, n, p->oz_S, p->oz_cexp, p->oz_planes, p->stream));
-    TRY(ozaki_gram(p->oz_maps, p->cm, n, p->oz_S, p->oz_cexp, p->oz_partial, dW, ldw, p->st, p->stream));
+    TRY(ozaki_gram(p->oz_maps, p->cm, n, p->oz_S, p->oz_cexp, p->oz_partial, p->oz_cap, dW, ldw, p->st, p->stream));
     return CQR2_OK;
   }
   TRY(gram_partials(dA, lda, p->cm, (int)p->n, p->g, p->partial, p->stream));
@@ -703,19 +724,15 @@ cqr2_status_t cqr2_factor_host(cqr2_plan_t p, const double* hA, int64_t lda, dou
       return CQR2_ERR_OOM;
     }
   }
-  const size_t rowb = (size_t)p->m * sizeof(double);
   {
     Stage st(p, CQR2_STAGE_H2D);
-    TRY(cudaMemcpy2DAsync(p->hA_dev, rowb, hA, (size_t)lda * sizeof(double), rowb, (size_t)p->n,
-                          cudaMemcpyHostToDevice, p->stream));
+    TRY(copy_cols(p->hA_dev, p->m, hA, lda, p->m, p->n, cudaMemcpyHostToDevice, p->stream));
   }
   if ((r = factor_any(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n)) != CQR2_OK) return r;
   {
     Stage st(p, CQR2_STAGE_D2H);
-    TRY(cudaMemcpy2DAsync(hQ, (size_t)ldq * sizeof(double), p->hQ_dev, rowb, rowb, (size_t)p->n,
-                          cudaMemcpyDeviceToHost, p->stream));
-    TRY(cudaMemcpy2DAsync(hR, (size_t)ldr * sizeof(double), p->hR_dev, (size_t)p->n * sizeof(double),
-                          (size_t)p->n * sizeof(double), (size_t)p->n, cudaMemcpyDeviceToHost, p->stream));
+    TRY(copy_cols(hQ, ldq, p->hQ_dev, p->m, p->m, p->n, cudaMemcpyDeviceToHost, p->stream));
+    TRY(copy_cols(hR, ldr, p->hR_dev, p->n, p->n, p->n, cudaMemcpyDeviceToHost, p->stream));
   }
   cqr2_info_t local;
   r = read_info(p, info ? info : &local);

@@ -89,7 +89,7 @@ constexpr int OZAKI_MAX_N = 1024;
 struct OzGeom {
   int64_t mp = 0;            // m rounded up to 64
   int np = 0;                // n rounded up to 64
-  int ntile_j = 0;           // 64-column tiles
+  int ntile_j = 0;           // Gram: 64-column tiles
   int ntiles = 0;            // Gram tiles (128 x 64) touching the upper triangle
   int64_t rows_per_split = 0;
   int nsplit = 0;
@@ -103,6 +103,8 @@ struct OzMaps {
 };
 bool ozaki_supported(int n, int S);
 OzGeom ozaki_geometry(int64_t m, int n);
+// Upper bound on ozaki_geometry(m', n).nsplit for every m' <= m.
+int64_t ozaki_split_capacity(int64_t m, int n);
 size_t ozaki_plane_elems(int64_t m, int n, int S);
 cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes, void* rinv_planes);
 cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned long long* colmax, int* cexp,
@@ -113,8 +115,9 @@ cudaError_t ozaki_slice_rows(const double* X, int64_t ld, int64_t m, int n, int 
                              cudaStream_t s);
 cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, unsigned short* planes,
                              int* fexp, cudaStream_t s);
-cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial, double* W,
-                       int64_t ldw, DevStatus* st, cudaStream_t s);
+// partial holds max_splits n x n blocks; a geometry needing more is refused.
+cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
+                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s);
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* rexp, const int* fexp, double* Q,
                         int64_t ldq, DevStatus* st, cudaStream_t s);
 

@@ -1,0 +1,87 @@
+// Fixed-point accumulator -> FP64 conversion of the split-precision path,
+// with integer operations only (GB300's FP64 pipe is far too slow even for
+// conversions). Host-compilable, so the rounding can be checked on the CPU
+// against exact rational arithmetic.
+#pragma once
+
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define OZ_HD __host__ __device__ __forceinline__
+#else
+#define OZ_HD inline
+#endif
+
+namespace cqr2 {
+
+OZ_HD int oz_clz64(unsigned long long x) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+OZ_HD double oz_bits_to_double(unsigned long long b) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+
+// Exact value m 2^e (m < 2^53) rounded into the subnormal range (or zero),
+// for the rare results below the normal range. Round to nearest, ties to even.
+OZ_HD double oz_scale_small(unsigned long long mant53, unsigned long long sticky_in, int e) {
+  // result bits = round(mant53 2^(e + 1074)); e + 1074 < 0 here
+  const int sh = -(e + 1074);
+  if (sh >= 64) return 0.0;
+  const unsigned long long q = mant53 >> sh;
+  const unsigned long long r = mant53 & ((1ull << sh) - 1ull);
+  const unsigned long long halfv = 1ull << (sh - 1);
+  const bool up = r > halfv || (r == halfv && (sticky_in || (q & 1ull)));
+  return oz_bits_to_double(q + (up ? 1ull : 0ull));
+}
+
+// (hi 2^32 + lo) 2^E rounded to the nearest double, ties to even, for
+// |hi|, |lo| < 2^62 (the accumulators of 2^20 rows stay far below that).
+OZ_HD double oz_fixed_to_double(long long hi, long long lo, int E) {
+  // T = H 2^32 + L with 0 <= L < 2^32
+  const long long H = hi + (lo >> 32);
+  const unsigned L = (unsigned)(unsigned long long)lo;
+  const bool neg = H < 0;
+  // |T| = W 2^32 + w0
+  const unsigned w0 = neg ? 0u - L : L;
+  const unsigned long long W = neg ? ~(unsigned long long)H + (L == 0u ? 1ull : 0ull) : (unsigned long long)H;
+  unsigned long long hw = W, lw = (unsigned long long)w0 << 32;
+  int top = 95;  // bit of |T| that bit 63 of hw holds
+  if (hw == 0) {
+    hw = lw;
+    lw = 0;
+    top = 31;
+  }
+  if (hw == 0) return 0.0;
+  const int lz = oz_clz64(hw);
+  const unsigned long long N = (hw << lz) | (lw >> 1 >> (63 - lz));  // top 64 bits, bit 63 set
+  const unsigned long long rest = lw << lz;                           // bits below N
+  const int msb = top - lz;                                            // |T| in [2^msb, 2^(msb+1))
+  unsigned long long mant = N >> 11;                                   // 53 bits, bit 52 set
+  const unsigned long long halfbit = (N >> 10) & 1ull;
+  const unsigned long long sticky = ((N & 0x3FFull) | rest) != 0 ? 1ull : 0ull;
+  const int biased = msb + E + 1023;
+  if (biased < 1) {
+    const double mag = oz_scale_small(mant, halfbit | sticky, msb + E - 52);
+    return neg ? -mag : mag;
+  }
+  mant += halfbit & (sticky | (mant & 1ull));
+  // the implicit bit adds one to the exponent field; a rounding carry to
+  // 2^53 moves it one further, as it must
+  unsigned long long bits = ((unsigned long long)(biased - 1) << 52) + mant;
+  if (biased > 2046) bits = 0x7FF0000000000000ull;  // overflow to infinity
+  return oz_bits_to_double(bits | (neg ? 1ull << 63 : 0ull));
+}
+
+}  // namespace cqr2

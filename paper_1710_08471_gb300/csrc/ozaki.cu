@@ -22,26 +22,24 @@
 // is the one of x' and the final conversion to FP64, done with integer
 // operations.
 //
-// Kernel: 128 x 64 output tile per CTA, BF16 operands K-major in 128-byte
-// swizzled shared memory, loaded by TMA (3-D maps over [slice][row][k]).
-// Warp 0 produces (TMA), warp 1 issues tcgen05.mma (M=128, N=64, K=16) into
-// the 7 group accumulators (448 TMEM columns), warps 2-9 drain groups. All
-// waits are bounded; a timeout sets the status word and the CTA unwinds.
+// Kernel: persistent, one CTA per SM, 128 x 32 output tiles, BF16 operands
+// K-major in 128-byte swizzled shared memory, loaded by TMA (3-D maps over
+// [slice][row][k]). Warp 0 produces (TMA), warp 1 issues tcgen05.mma (M=128,
+// one MMA of N = 32 (S - s) per A slice s and K=16 step) into S group
+// accumulators of 32 TMEM columns, double buffered, and warps 2-9 drain them.
+// All waits are bounded; a timeout sets the status word and the CTA unwinds.
 #include <cuda.h>
 
 #include <algorithm>
 
 #include "kernels.h"
+#include "oz_fixed.cuh"
 
 namespace cqr2 {
 namespace {
 
 constexpr int OZ_BK = 64;          // contraction per K-block (128-byte rows)
 constexpr int OZ_BM = 128;         // tile rows
-constexpr int OZ_BN = 64;          // tile columns
-constexpr int OZ_NA = 4;           // A-plane ring slots
-constexpr int OZ_THREADS = 320;    // producer + MMA + 8 epilogue warps
-constexpr int OZ_EPI_WARPS = 8;
 constexpr int EXP_NONFINITE = 1 << 20;  // exponent sentinel: a non-finite entry was seen
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
@@ -79,74 +77,51 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int S) {
   return (b >> 63) ? -v : v;
 }
 
-__device__ __forceinline__ unsigned short small_int_to_bf16(int d) {
-  if (d == 0) return 0;
-  const unsigned s = d < 0 ? 0x8000u : 0u;
-  const unsigned a = (unsigned)(d < 0 ? -d : d);
-  const int msb = 31 - __clz(a);
-  const unsigned frac = (a << (7 - msb)) & 0x7Fu;
-  return (unsigned short)(s | ((unsigned)(127 + msb) << 7) | frac);
+// BF16 bits of a small integer |d| <= 2^8: placing d in the low mantissa
+// bits of 1.5 * 2^23 and subtracting 1.5 * 2^23 gives d exactly in FP32 (one
+// integer add, one FP32 add); with at most 8 significant bits its low 16 bits
+// are zero, so the top half is the exact BF16 value.
+__device__ __forceinline__ unsigned small_int_to_bf16(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// The S digits of x (shared exponent e) as BF16 bits, most significant first.
+template <int S>
+__device__ __forceinline__ void digits_bf16(double x, int e, unsigned (&out)[S]) {
+  long long v = to_fixed(x, e, S);
+#pragma unroll
+  for (int s = S - 1; s >= 1; --s) {
+    const int lo = (int)(signed char)(v & 0xFF);
+    out[s] = small_int_to_bf16(lo);
+    v = (v - lo) >> 8;
+  }
+  out[0] = small_int_to_bf16((int)v);
 }
 
 // Writes the S digits of x (with shared exponent e) as BF16 to out[s * stride].
 template <int S>
 __device__ __forceinline__ void write_digits(double x, int e, unsigned short* out, size_t stride) {
-  long long v = to_fixed(x, e, S);
-  int d[S];
+  unsigned d[S];
+  digits_bf16<S>(x, e, d);
 #pragma unroll
-  for (int s = S - 1; s >= 1; --s) {
-    const int lo = (int)(signed char)(v & 0xFF);
-    d[s] = lo;
-    v = (v - lo) >> 8;
-  }
-  d[0] = (int)v;
-#pragma unroll
-  for (int s = 0; s < S; ++s) out[(size_t)s * stride] = small_int_to_bf16(d[s]);
+  for (int s = 0; s < S; ++s) out[(size_t)s * stride] = (unsigned short)d[s];
 }
 
-// value = (hi * 2^32 + lo) * 2^E, rounded to nearest, with integer operations.
-__device__ __forceinline__ double fixed_to_double(long long hi, long long lo, int E) {
-  unsigned long long l = (unsigned long long)lo + ((unsigned long long)hi << 32);
-  const unsigned long long c = l < (unsigned long long)lo ? 1ull : 0ull;
-  unsigned long long h = (unsigned long long)((lo >> 63) + (hi >> 32)) + c;
-  const bool neg = (long long)h < 0;
-  if (neg) {
-    l = ~l + 1ull;
-    h = ~h + (l == 0 ? 1ull : 0ull);
+// Digits of four consecutive entries, written as one 8-byte store per slice.
+template <int S>
+__device__ __forceinline__ void write_digits4(const double (&x)[4], const int (&e)[4], unsigned short* out,
+                                              size_t stride) {
+  unsigned d[4][S];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) digits_bf16<S>(x[q], e[q], d[q]);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    uint2 w;
+    w.x = d[0][s] | (d[1][s] << 16);
+    w.y = d[2][s] | (d[3][s] << 16);
+    *reinterpret_cast<uint2*>(out + (size_t)s * stride) = w;
   }
-  if (h == 0 && l == 0) return 0.0;
-  const int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)l);
-  unsigned long long th, tl;
-  if (lz >= 64) {
-    th = l << (lz - 64);
-    tl = 0;
-  } else if (lz > 0) {
-    th = (h << lz) | (l >> (64 - lz));
-    tl = l << lz;
-  } else {
-    th = h;
-    tl = l;
-  }
-  int msb = 127 - lz;
-  unsigned long long m = th >> 11;
-  const bool round = (th >> 10) & 1ull;
-  const bool sticky = ((th & 0x3FFull) != 0) || (tl != 0);
-  if (round && (sticky || (m & 1ull))) {
-    m += 1;
-    if (m >> 53) {
-      m >>= 1;
-      msb += 1;
-    }
-  }
-  const int biased = msb + E + 1023;
-  if (biased <= 0 || biased >= 2047) {
-    // outside the normal range: rare, use FP64 arithmetic
-    const double mag = ldexp((double)m, msb - 52 + E);
-    return neg ? -mag : mag;
-  }
-  const unsigned long long bits =
-      (neg ? (1ull << 63) : 0ull) | ((unsigned long long)biased << 52) | (m & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
 }
 
 // ------------------------------------------------------------ slicing kernels
@@ -187,34 +162,43 @@ template <int S>
 __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ X, int64_t ld, int64_t m, int n,
                                                     int64_t mp, const int* __restrict__ cexp,
                                                     unsigned short* __restrict__ planes) {
+  // four consecutive rows per thread: 32 contiguous bytes read, one 8-byte
+  // store per slice (mp is a multiple of 64)
   const int j = blockIdx.y;
   const int e = cexp[j];
+  const int ee[4] = {e, e, e, e};
   const size_t stride = (size_t)n * mp;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < mp; k += (int64_t)gridDim.x * blockDim.x) {
-    const double x = k < m ? X[k + (int64_t)j * ld] : 0.0;
-    write_digits<S>(x, e, planes + (size_t)j * mp + k, stride);
+  const double* col = X + (int64_t)j * ld;
+  for (int64_t k = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); k < mp;
+       k += 4 * (int64_t)gridDim.x * blockDim.x) {
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = k + q < m ? col[k + q] : 0.0;
+    write_digits4<S>(x, ee, planes + (size_t)j * mp + k, stride);
   }
 }
 
 // Row slices for the Q-form's left operand: planes[s][r][k], k < np, with one
-// exponent per row. A CTA stages 16 rows x n in shared memory.
-constexpr int SR_ROWS = 16;
-template <int S>
+// exponent per row. A CTA stages RB rows x n in shared memory (read
+// coalesced down the columns), finds each row's largest entry, and writes
+// four consecutive k per thread (one 8-byte store per slice).
+template <int S, int RB>
 __global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ X, int64_t ld, int64_t m, int n, int np,
                                                     unsigned short* __restrict__ planes, int* __restrict__ rexp) {
-  extern __shared__ double tile[];  // [n][SR_ROWS]
-  __shared__ int sexp[SR_ROWS];
-  const int64_t r0 = (int64_t)blockIdx.x * SR_ROWS;
-  for (int e = threadIdx.x; e < n * SR_ROWS; e += blockDim.x) {
-    const int r = e % SR_ROWS, k = e / SR_ROWS;
-    tile[e] = (r0 + r < m) ? X[r0 + r + (int64_t)k * ld] : 0.0;
+  extern __shared__ double tile[];  // [n][RB + 1]
+  __shared__ int sexp[RB];
+  constexpr int LDT = RB + 1;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
+    const int r = e % RB, k = e / RB;
+    tile[k * LDT + r] = (r0 + r < m) ? X[r0 + r + (int64_t)k * ld] : 0.0;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < SR_ROWS; r += 8) {
+  for (int r = warp; r < RB; r += 8) {
     unsigned long long mx = 0;
     for (int k = lane; k < n; k += 32) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(tile[k * SR_ROWS + r]) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(tile[k * LDT + r]) & 0x7FFFFFFFFFFFFFFFull;
       mx = b > mx ? b : mx;
     }
 #pragma unroll
@@ -229,11 +213,18 @@ __global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ X
   }
   __syncthreads();
   const size_t stride = (size_t)m * np;
-  for (int e = threadIdx.x; e < SR_ROWS * np; e += blockDim.x) {
-    const int r = e / np, k = e % np;
+  const int q4 = np / 4;
+  for (int e = threadIdx.x; e < RB * q4; e += blockDim.x) {
+    const int r = e / q4, k = 4 * (e % q4);
     if (r0 + r >= m) continue;
-    const double x = k < n ? tile[k * SR_ROWS + r] : 0.0;
-    write_digits<S>(x, sexp[r], planes + (size_t)(r0 + r) * np + k, stride);
+    double x[4];
+    int ex[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x[q] = k + q < n ? tile[(k + q) * LDT + r] : 0.0;
+      ex[q] = sexp[r];
+    }
+    write_digits4<S>(x, ex, planes + (size_t)(r0 + r) * np + k, stride);
   }
 }
 
@@ -331,14 +322,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -347,11 +335,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 enum { OZ_GRAM = 0, OZ_QFORM = 1 };
 
+// Tile shapes. The Gram uses 128 x 64 tiles (more operand reuse; the S group
+// accumulators take 64 S <= 448 TMEM columns, one buffer). The Q-form uses
+// 128 x 32 tiles with two accumulator buffers (2 x 32 S <= 448 columns) and
+// 16 epilogue warps, since its epilogue (one conversion per output) is as
+// long as its MMAs.
+constexpr int OZ_GRAM_BN = 64, OZ_GRAM_EPI = 8;
+constexpr int OZ_QFORM_BN = 32, OZ_QFORM_EPI = 16;
+
+template <int S, int BN, int EPI>
+struct OzCfg {
+  static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;         // accumulator buffers in TMEM
+  static constexpr int THREADS = 64 + 32 * EPI;                   // producer, MMA, epilogue warps
+  static constexpr int A_BYTES = OZ_BM * OZ_BK * 2;               // one A slice tile
+  static constexpr int B_BYTES = BN * OZ_BK * 2;                  // one B slice tile
+  static constexpr int NA = (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES < 8
+                                ? (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES
+                                : 8;                              // A ring slots
+  static constexpr int CPT = BN / (EPI / 4);                      // columns per epilogue thread
+  static constexpr int TMAX = 256 / BN;                           // products per MMA (N <= 256)
+  static constexpr int NBAR = 2 * NA + 4 + 2 * NBUF * S;
+  static constexpr size_t SMEM = 1024 + (size_t)NA * A_BYTES + (size_t)2 * S * B_BYTES + 8 * NBAR + 16;
+  static_assert(NBUF * S * BN <= 512, "accumulators must fit in TMEM");
+  static_assert(CPT == 8 || CPT == 16 || CPT == 32, "epilogue load width");
+  static_assert(NA >= S, "a K-block of A slices must fit the ring");
+};
+
 struct OzParams {
   int64_t m;
   int n;
   int64_t rows_per_split;  // Gram: rows per CTA range (multiple of 128)
-  int ntile_j;             // number of 64-column tiles, ceil(n / 64)
+  int ntile_j;             // column tiles, ceil(n / BN)
+  int ntiles;              // Gram: tiles touching the upper triangle
+  int64_t nitems;          // work items (tiles x row ranges, or output tiles)
   const int* eA;           // Gram: column exponents; Q-form: row exponents of X
   const int* eB;           // Gram: column exponents; Q-form: column exponents of R^-1
   double* out;             // Gram: partial[split][n][n]; Q-form: Q
@@ -359,56 +375,148 @@ struct OzParams {
   DevStatus* st;
 };
 
-template <int S, int MODE>
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(const __grid_constant__ CUtensorMap tA,
-                                                               const __grid_constant__ CUtensorMap tB, OzParams p) {
-  constexpr int A_BYTES = OZ_BM * OZ_BK * 2;
-  constexpr int B_BYTES = OZ_BN * OZ_BK * 2;
+// One work item: an output tile and its contraction range.
+struct OzItem {
+  int64_t i0, j0, kbase;
+  int nk;     // K-blocks of 64
+  int split;  // Gram: row range
+};
+
+// K-blocks of a Q-form tile with first column j0: R^-1 is upper triangular,
+// so only k < j0 + BN contributes.
+template <int BN>
+__device__ __forceinline__ int oz_qform_nk(int64_t j0, int n) {
+  return min((int)((j0 + BN + OZ_BK - 1) / OZ_BK), (n + OZ_BK - 1) / OZ_BK);
+}
+
+template <int MODE, int BN>
+__device__ __forceinline__ OzItem oz_item(const OzParams& p, int64_t it) {
+  OzItem w;
+  constexpr int R = OZ_BM / BN;  // column tiles per 128-row block
+  if (MODE == OZ_GRAM) {
+    // the tiles of one row range are neighbours: their slices are shared in L2
+    int t = (int)(it % p.ntiles), I = 0;
+    w.split = (int)(it / p.ntiles);
+    while (t >= p.ntile_j - R * I) {
+      t -= p.ntile_j - R * I;
+      ++I;
+    }
+    w.i0 = (int64_t)OZ_BM * I;
+    w.j0 = (int64_t)BN * (R * I + t);
+    w.kbase = (int64_t)w.split * p.rows_per_split;
+    const int64_t kend = min(p.m, w.kbase + p.rows_per_split);
+    w.nk = kend > w.kbase ? (int)((kend - w.kbase + OZ_BK - 1) / OZ_BK) : 0;
+  } else {
+    // the column tiles of one row tile are neighbours: they share A slices in L2
+    w.j0 = (int64_t)BN * (it % p.ntile_j);
+    w.i0 = (int64_t)OZ_BM * (it / p.ntile_j);
+    w.kbase = 0;
+    w.split = 0;
+    w.nk = oz_qform_nk<BN>(w.j0, p.n);
+  }
+  return w;
+}
+
+// First work item of CTA b of G (CTA G gives the end). Each CTA takes a
+// contiguous range of items. Gram items cost the same, so the ranges hold
+// equal counts. A Q-form item costs its K-blocks plus a fixed epilogue (model:
+// nk + 1); the ranges split the total cost evenly, so that no CTA is left with
+// only the widest tiles.
+template <int MODE, int BN>
+__device__ __forceinline__ int64_t oz_range_begin(const OzParams& p, int64_t b, int64_t G) {
+  if (MODE == OZ_GRAM) return b * p.nitems / G;
+  const int J = p.ntile_j;
+  int64_t P = 0;  // cost of one row tile
+  for (int j = 0; j < J; ++j) P += oz_qform_nk<BN>((int64_t)BN * j, p.n) + 1;
+  const int64_t rows = p.nitems / J;
+  const int64_t target = b * (rows * P) / G;  // cost before the range
+  const int64_t rt = target / P;
+  int64_t rem = target - rt * P;
+  int j = 0;
+  while (j < J && rem > 0) {
+    rem -= oz_qform_nk<BN>((int64_t)BN * j, p.n) + 1;
+    ++j;
+  }
+  return rt * J + j;
+}
+
+// acc += x * w in one integer multiply-add (32 x 32 -> 64 bits).
+__device__ __forceinline__ void mad_wide(long long& acc, int x, int w) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(w));
+}
+
+// Adds the group sums of one chunk (exact integers in FP32) into the two
+// fixed-point accumulators: groups 0-2 into hi with weights 2^16, 2^8, 1,
+// groups 3-6 into lo with weights 2^24 .. 1.
+template <int G, int N>
+__device__ __forceinline__ void oz_accumulate(const uint32_t* v, long long* hi, long long* lo) {
+  constexpr int W = G <= 2 ? 1 << (8 * (2 - G)) : 1 << (8 * (6 - G));
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) {
+    const int x = __float2int_rn(__uint_as_float(v[cc]));
+    if (G <= 2) mad_wide(hi[cc], x, W);
+    else mad_wide(lo[cc], x, W);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
+  uint32_t(&w)[16] = *reinterpret_cast<uint32_t(*)[16]>(v);
+  tmem_ld16(taddr, w);
+}
+
+// Drains group G of one chunk for this thread's CPT columns (16 at a time).
+template <int G, int CPT>
+__device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* hi, long long* lo) {
+  constexpr int W = CPT < 16 ? CPT : 16;
+#pragma unroll
+  for (int h = 0; h < CPT / W; ++h) {
+    uint32_t v[W];
+    tmem_ld<W>(ta + W * h, v);
+    oz_accumulate<G, W>(v, hi + W * h, lo + W * h);
+  }
+}
+
+// Persistent: CTA b takes the items of its range in order. The producer, the
+// MMA issuer and the epilogue walk the same item sequence with running
+// counters (K-blocks, A slices, chunks), so the mbarrier phases continue
+// across items. Group g of chunk c lives in accumulator buffer c % NBUF; the
+// epilogue drains a group as soon as its last product is done and the MMAs
+// overwrite it only after that drain. Warp w of the epilogue reads TMEM lanes
+// 32 (w % 4) .. +31 (its rows) and one column slice of each group.
+template <int S, int MODE, int BN, int EPI>
+__global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
+    k_ozaki_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzParams p) {
+  using C = OzCfg<S, BN, EPI>;
+  constexpr int NA = C::NA, NBUF = C::NBUF, CPT = C::CPT;
+  constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+  constexpr uint32_t ACC_COLS = S * BN;  // one accumulator buffer
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;                              // OZ_NA slots
-  uint8_t* sB = sA + OZ_NA * A_BYTES;              // 2 buffers x S planes
+  uint8_t* sA = smem;                  // NA slots
+  uint8_t* sB = sA + NA * A_BYTES;     // 2 buffers x S planes
   uint64_t* bar = (uint64_t*)(sB + 2 * S * B_BYTES);
   uint64_t* afull = bar;
-  uint64_t* aempty = afull + OZ_NA;
-  uint64_t* bfull = aempty + OZ_NA;
+  uint64_t* aempty = afull + NA;
+  uint64_t* bfull = aempty + NA;
   uint64_t* bempty = bfull + 2;
-  uint64_t* accfull = bempty + 2;
-  uint64_t* accempty = accfull + S;
-  uint32_t* tmem_slot = (uint32_t*)(accempty + S);
+  uint64_t* accfull = bempty + 2;       // [NBUF][S]
+  uint64_t* accempty = accfull + NBUF * S;
+  uint32_t* tmem_slot = (uint32_t*)(accempty + NBUF * S);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // Tile and contraction range.
-  int64_t i0, j0, kbase;
-  int nk;
-  int split = 0;
-  if (MODE == OZ_GRAM) {
-    int t = blockIdx.x, I = 0;
-    while (t >= p.ntile_j - 2 * I) {
-      t -= p.ntile_j - 2 * I;
-      ++I;
-    }
-    i0 = (int64_t)OZ_BM * I;
-    j0 = (int64_t)OZ_BN * (2 * I + t);
-    split = blockIdx.y;
-    kbase = (int64_t)split * p.rows_per_split;
-    const int64_t kend = min(p.m, kbase + p.rows_per_split);
-    nk = kend > kbase ? (int)((kend - kbase + OZ_BK - 1) / OZ_BK) : 0;
-  } else {
-    // 1-D grid: the column tiles of one row tile are neighbours, so the A
-    // slices they share are read once from memory and then from L2.
-    const int64_t lin = (int64_t)blockIdx.x;
-    j0 = (int64_t)OZ_BN * (lin % p.ntile_j);
-    i0 = (int64_t)OZ_BM * (lin / p.ntile_j);
-    kbase = 0;
-    nk = (int)((j0 + OZ_BN + OZ_BK - 1) / OZ_BK);  // R^-1 upper triangular: k < j0 + 64
-    const int nkmax = (p.n + OZ_BK - 1) / OZ_BK;
-    nk = min(nk, nkmax);
-  }
-
   if (threadIdx.x == 0) {
-    for (int i = 0; i < OZ_NA; ++i) {
+    for (int i = 0; i < NA; ++i) {
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 1);
     }
@@ -416,9 +524,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(const __grid_const
       mbar_init(&bfull[i], 1);
       mbar_init(&bempty[i], 1);
     }
-    for (int g = 0; g < S; ++g) {
-      mbar_init(&accfull[g], 1);
-      mbar_init(&accempty[g], OZ_EPI_WARPS);
+    for (int i = 0; i < NBUF * S; ++i) {
+      mbar_init(&accfull[i], 1);
+      mbar_init(&accempty[i], EPI);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -431,136 +539,142 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(const __grid_const
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
+  const int64_t it_begin = oz_range_begin<MODE, BN>(p, blockIdx.x, gridDim.x);
+  const int64_t it_end = oz_range_begin<MODE, BN>(p, blockIdx.x + 1, gridDim.x);
 
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
-      for (int kb = 0; kb < nk && ok; ++kb) {
-        const int buf = kb & 1;
-        const int k0 = (int)(kbase + (int64_t)kb * OZ_BK);
-        if (kb >= 2) ok = mbar_wait(&bempty[buf], ((kb >> 1) - 1) & 1, p.st);
-        if (!ok) break;
-        mbar_expect_tx(&bfull[buf], S * B_BYTES);
-        for (int t = 0; t < S; ++t) tma_load_3d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], k0, (int)j0, t);
-        for (int s = 0; s < S; ++s) {
-          const int q = kb * S + s, slot = q % OZ_NA;
-          if (q >= OZ_NA) ok = mbar_wait(&aempty[slot], ((q / OZ_NA) - 1) & 1, p.st);
+      int64_t gk = 0, q = 0;  // running K-block and A-slice counters
+      for (int64_t it = it_begin; it < it_end && ok; ++it) {
+        const OzItem w = oz_item<MODE, BN>(p, it);
+        for (int kb = 0; kb < w.nk && ok; ++kb, ++gk) {
+          const int buf = (int)(gk & 1);
+          const int k0 = (int)(w.kbase + (int64_t)kb * OZ_BK);
+          if (gk >= 2) ok = mbar_wait(&bempty[buf], (uint32_t)(((gk >> 1) - 1) & 1), p.st);
           if (!ok) break;
-          mbar_expect_tx(&afull[slot], A_BYTES);
-          tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)i0, s);
+          mbar_expect_tx(&bfull[buf], S * B_BYTES);
+          for (int t = 0; t < S; ++t)
+            tma_load_3d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], k0, (int)w.j0, t);
+          for (int s = 0; s < S; ++s, ++q) {
+            const int slot = (int)(q % NA);
+            if (q >= NA) ok = mbar_wait(&aempty[slot], (uint32_t)(((q / NA) - 1) & 1), p.st);
+            if (!ok) break;
+            mbar_expect_tx(&afull[slot], A_BYTES);
+            tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)w.i0, s);
+          }
         }
       }
       if (!ok) report_timeout(p.st);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                             ((uint32_t)(OZ_BM >> 4) << 24);
+      // kind::f16, BF16 A and B, FP32 accumulate, both K-major, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
       bool ok = true;
-      for (int kb = 0; kb < nk && ok; ++kb) {
-        const int buf = kb & 1;
-        const bool first = (kb & 1) == 0;
-        const bool last = (kb & 1) == 1 || kb == nk - 1;
-        const int c = kb >> 1;
-        ok = mbar_wait(&bfull[buf], (kb >> 1) & 1, p.st);
-        if (!ok) break;
-        for (int s = 0; s < S && ok; ++s) {
-          const int q = kb * S + s, slot = q % OZ_NA;
-          ok = mbar_wait(&afull[slot], (q / OZ_NA) & 1, p.st);
+      int64_t gk = 0, q = 0, gc = 0;  // running K-block, A-slice and chunk counters
+      for (int64_t it = it_begin; it < it_end && ok; ++it) {
+        const OzItem w = oz_item<MODE, BN>(p, it);
+        for (int kb = 0; kb < w.nk && ok; ++kb, ++gk) {
+          const int buf = (int)(gk & 1);
+          const bool first = (kb & 1) == 0;
+          const bool last = (kb & 1) == 1 || kb == w.nk - 1;
+          const int ab = (int)(gc % NBUF);   // accumulator buffer of this chunk
+          const int64_t use = gc / NBUF;     // earlier chunks in this buffer
+          const uint32_t acc = tmem + (uint32_t)ab * ACC_COLS;
+          ok = mbar_wait(&bfull[buf], (uint32_t)((gk >> 1) & 1), p.st);
           if (!ok) break;
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint64_t da = sdesc(sA + slot * A_BYTES);
-          // Products (s, t) for t = t0 .. t0+nt-1 in one MMA of N = 64 nt: the
-          // B slices lie back to back in shared memory (one 1024-byte group
-          // pitch throughout) and the groups g = s + t are adjacent 64-column
-          // accumulators in TMEM, so the wide MMA lands every product in its
-          // own group.
-          for (int t0 = 0; t0 + s < S && ok; t0 += 4) {
-            const int nt = min(4, S - s - t0);
-            if (first && s == 0 && c >= 1) {
-              for (int g = t0; g < t0 + nt && ok; ++g) ok = mbar_wait(&accempty[g], (c - 1) & 1, p.st);
-              if (!ok) break;
-              asm volatile("tcgen05.fence::after_thread_sync;");
-            }
-            const uint32_t idesc_n = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((OZ_BN * nt) >> 3) << 17);
-            const uint64_t db = sdesc(sB + (buf * S + t0) * B_BYTES);
+          for (int s = 0; s < S && ok; ++s, ++q) {
+            const int slot = (int)(q % NA);
+            ok = mbar_wait(&afull[slot], (uint32_t)((q / NA) & 1), p.st);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t da = sdesc(sA + slot * A_BYTES);
+            // Products (s, t), t = t0 .. t0+nt-1, in one MMA of N = BN nt: the
+            // B slices lie back to back in shared memory (one 1024-byte pitch
+            // per 8 rows throughout) and group g = s + t is the BN-column
+            // accumulator at column BN g, so each product lands in its group.
+            for (int t0 = 0; t0 + s < S && ok; t0 += C::TMAX) {
+              const int nt = min(C::TMAX, S - s - t0);
+              if (first && s == 0 && use >= 1) {  // the first write of groups t0.. in this buffer
+                for (int g = t0; g < t0 + nt && ok; ++g)
+                  ok = mbar_wait(&accempty[ab * S + g], (uint32_t)((use - 1) & 1), p.st);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+              }
+              const uint32_t idesc_n = idesc | ((uint32_t)((BN * nt) >> 3) << 17);
+              const uint64_t db = sdesc(sB + (buf * S + t0) * B_BYTES);
 #pragma unroll
-            for (int k = 0; k < OZ_BK / 16; ++k)
-              mma_bf16(tmem + (uint32_t)((s + t0) * OZ_BN), da + 2 * k, db + 2 * k, idesc_n,
-                       (first && s == 0 && k == 0) ? 0u : 1u);
+              for (int k = 0; k < OZ_BK / 16; ++k)
+                mma_bf16(acc + (uint32_t)((s + t0) * BN), da + 2 * k, db + 2 * k, idesc_n,
+                         (first && s == 0 && k == 0) ? 0u : 1u);
+            }
+            if (!ok) break;
+            mma_commit(&aempty[slot]);
+            if (last) mma_commit(&accfull[ab * S + s]);  // every product of group s is issued
           }
-          mma_commit(&aempty[slot]);
-          if (last) mma_commit(&accfull[s]);  // every product of group s is issued
+          if (!ok) break;
+          mma_commit(&bempty[buf]);
+          if (last) ++gc;
         }
-        mma_commit(&bempty[buf]);
       }
       if (!ok) report_timeout(p.st);
     }
   } else {
-    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns half*32 .. +31.
     const int q4 = warp & 3;
-    const int half = (warp - 2) >> 2;
-    long long hi[32], lo[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0;
-    const int nchunks = (nk + 1) >> 1;
+    const int cs = (warp - 2) >> 2;  // column slice of each group
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-#pragma unroll 1
-      for (int g = 0; g < S; ++g) {
-        ok = mbar_wait(&accfull[g], c & 1, p.st);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * OZ_BN + half * 32), v);
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&accempty[g]);
-        if (g <= 2) {
-          const int sh = 8 * (2 - g);
+    int64_t gc = 0;
+    for (int64_t it = it_begin; it < it_end && ok; ++it) {
+      const OzItem w = oz_item<MODE, BN>(p, it);
+      long long hi[CPT], lo[CPT];
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc)
-            hi[cc] += (long long)((unsigned long long)(long long)__float2int_rn(__uint_as_float(v[cc])) << sh);
-        } else {
-          const int sh = 8 * (6 - g);
+      for (int c = 0; c < CPT; ++c) hi[c] = lo[c] = 0;
+      const int nchunks = (w.nk + 1) >> 1;
+      for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+        const int ab = (int)(gc % NBUF);
+        const uint32_t par = (uint32_t)((gc / NBUF) & 1);
+        const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)ab * ACC_COLS + (uint32_t)(cs * CPT);
+#define OZ_DRAIN(G)                                                        \
+  if (G < S && ok) {                                                       \
+    ok = mbar_wait(&accfull[ab * S + G], par, p.st);                       \
+    if (ok) {                                                              \
+      asm volatile("tcgen05.fence::after_thread_sync;");                   \
+      oz_drain_group<G, CPT>(ta + G * BN, hi, lo);                         \
+      asm volatile("tcgen05.fence::before_thread_sync;");                  \
+      __syncwarp();                                                        \
+      if (lane == 0) mbar_arrive(&accempty[ab * S + G]);                   \
+    }                                                                      \
+  }
+        OZ_DRAIN(0)
+        OZ_DRAIN(1)
+        OZ_DRAIN(2)
+        OZ_DRAIN(3)
+        OZ_DRAIN(4)
+        OZ_DRAIN(5)
+        OZ_DRAIN(6)
+#undef OZ_DRAIN
+      }
+      if (!ok) break;
+      const int64_t row = w.i0 + q4 * 32 + lane;
+      const int64_t nrow = MODE == OZ_GRAM ? p.n : p.m;
+      if (row < nrow) {
+        const int ea = p.eA[row];
+        double* out = MODE == OZ_GRAM ? p.out + (int64_t)w.split * p.n * p.n : p.out;
+        const int64_t ld = MODE == OZ_GRAM ? p.n : p.ldo;
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc)
-            lo[cc] += (long long)((unsigned long long)(long long)__float2int_rn(__uint_as_float(v[cc])) << sh);
+        for (int cc = 0; cc < CPT; ++cc) {
+          const int64_t col = w.j0 + cs * CPT + cc;
+          if (col < p.n) {
+            const int eb = p.eB[col];
+            out[row + col * ld] = (ea >= EXP_NONFINITE || eb >= EXP_NONFINITE)
+                                      ? __longlong_as_double(0x7FF8000000000000ll)
+                                      : oz_fixed_to_double(hi[cc], lo[cc], ea + eb - 14 - 48);
+          }
         }
       }
     }
     if (!ok) report_timeout(p.st);
-    const int64_t row = i0 + q4 * 32 + lane;
-    if (MODE == OZ_GRAM) {
-      if (row < p.n) {
-        const int ea = p.eA[row];
-        double* out = p.out + (int64_t)split * p.n * p.n;
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-          const int64_t col = j0 + half * 32 + cc;
-          if (col < p.n) {
-            const int eb = p.eB[col];
-            double v = (ea >= EXP_NONFINITE || eb >= EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                    : fixed_to_double(hi[cc], lo[cc], ea + eb - 14 - 48);
-            out[row + col * p.n] = v;
-          }
-        }
-      }
-    } else {
-      if (row < p.m) {
-        const int ea = p.eA[row];
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-          const int64_t col = j0 + half * 32 + cc;
-          if (col < p.n) {
-            const int eb = p.eB[col];
-            double v = (ea >= EXP_NONFINITE || eb >= EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                    : fixed_to_double(hi[cc], lo[cc], ea + eb - 14 - 48);
-            p.out[row + col * p.ldo] = v;
-          }
-        }
-      }
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -599,50 +713,59 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int S>
-size_t oz_smem() {
-  return 1024 + (size_t)OZ_NA * OZ_BM * OZ_BK * 2 + (size_t)2 * S * OZ_BN * OZ_BK * 2 + 8 * (2 * OZ_NA + 4 + 2 * S) +
-         16;
-}
-
-template <int S, int MODE>
+template <int S, int MODE, int BN, int EPI>
 cudaError_t launch_oz(const CUtensorMap& a, const CUtensorMap& b, const OzParams& p, dim3 grid, cudaStream_t s) {
-  const size_t sm = oz_smem<S>();
-  auto kern = k_ozaki_gemm<S, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  using Cfg = OzCfg<S, BN, EPI>;
+  static_assert(Cfg::SMEM <= 227 * 1024, "shared memory per CTA");
+  auto kern = k_ozaki_gemm<S, MODE, BN, EPI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<grid, OZ_THREADS, sm, s>>>(a, b, p);
+  kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, b, p);
   count_launch();
   return cudaGetLastError();
 }
 
 }  // namespace
 
+int64_t sm_count_oz() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;  // one CTA per SM (shared memory and the 512 TMEM columns)
+}
+
 // ------------------------------------------------------------ public (internal) API
 
 bool ozaki_supported(int n, int S) { return n >= 1 && n <= OZAKI_MAX_N && S >= 6 && S <= 7; }
+
+namespace {
+constexpr int64_t OZ_MAX_CHUNKS_PER_SPLIT = (1 << 20) / 128;  // fixed-point headroom
+
+// About two waves of one CTA per SM over all tiles.
+int64_t oz_split_target(int ntiles) {
+  return std::max<int64_t>(1, ceil_div((int64_t)2 * sm_count_oz(), ntiles));
+}
+}  // namespace
 
 OzGeom ozaki_geometry(int64_t m, int n) {
   OzGeom g;
   g.mp = ceil_div(m, OZ_BK) * OZ_BK;
   g.np = (int)(ceil_div(n, OZ_BK) * OZ_BK);
-  g.ntile_j = (int)ceil_div(n, OZ_BN);
+  g.ntile_j = (int)ceil_div(n, OZ_GRAM_BN);
   g.ntiles = 0;
-  for (int I = 0; 2 * I < g.ntile_j; ++I) g.ntiles += g.ntile_j - 2 * I;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // one CTA per SM at a time; about two waves, ranges of at most 2^20 rows (fixed-point headroom)
-  int64_t want = std::max<int64_t>(1, ceil_div((int64_t)2 * sms, g.ntiles));
+  constexpr int R = OZ_BM / OZ_GRAM_BN;  // column tiles per 128-row block
+  for (int I = 0; R * I < g.ntile_j; ++I) g.ntiles += g.ntile_j - R * I;
+  // ranges of at most 2^20 rows (8192 chunks) keep the int64 accumulators exact
   const int64_t chunks = ceil_div(m, 128);
-  want = std::min<int64_t>(want, chunks);
+  const int64_t want = std::max(std::min(oz_split_target(g.ntiles), chunks), ceil_div(chunks, OZ_MAX_CHUNKS_PER_SPLIT));
   g.rows_per_split = ceil_div(chunks, want) * 128;
-  while (g.rows_per_split > (1 << 20)) {
-    ++want;
-    g.rows_per_split = ceil_div(chunks, want) * 128;
-  }
-  g.nsplit = (int)ceil_div(m, g.rows_per_split);
+  g.nsplit = (int)ceil_div(m, g.rows_per_split);  // <= want
   return g;
+}
+
+int64_t ozaki_split_capacity(int64_t m, int n) {
+  const OzGeom g = ozaki_geometry(m, n);
+  return std::max<int64_t>(oz_split_target(g.ntiles), ceil_div(ceil_div(m, 128), OZ_MAX_CHUNKS_PER_SPLIT));
 }
 
 size_t ozaki_plane_elems(int64_t m, int n, int S) {
@@ -665,9 +788,9 @@ cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes,
   };
   static_assert(sizeof(CUtensorMap) <= sizeof(OzMaps::col_a), "tensor map storage");
   bool ok = make((CUtensorMap*)maps.col_a, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BM) &&
-            make((CUtensorMap*)maps.col_b, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BN) &&
+            make((CUtensorMap*)maps.col_b, planes, (uint64_t)g.mp, (uint64_t)n, OZ_GRAM_BN) &&
             make((CUtensorMap*)maps.row_a, planes, (uint64_t)g.np, (uint64_t)m, OZ_BM) &&
-            make((CUtensorMap*)maps.rinv_b, rinv_planes, (uint64_t)g.np, (uint64_t)n, OZ_BN);
+            make((CUtensorMap*)maps.rinv_b, rinv_planes, (uint64_t)g.np, (uint64_t)n, OZ_QFORM_BN);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -687,9 +810,20 @@ cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned
 cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int S, const int* cexp,
                              unsigned short* planes, cudaStream_t s) {
   const OzGeom g = ozaki_geometry(m, n);
-  dim3 grid((unsigned)std::min<int64_t>(ceil_div(g.mp, 256), 1024), (unsigned)n);
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(g.mp, 4 * 256), 1024), (unsigned)n);
   if (S == 7) k_slice_cols<7><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes);
   else k_slice_cols<6><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int S, int RB>
+cudaError_t launch_slice_rows(const double* X, int64_t ld, int64_t m, int n, int np, unsigned short* planes, int* rexp,
+                              cudaStream_t s) {
+  const size_t sm = (size_t)n * (RB + 1) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_slice_rows<S, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_slice_rows<S, RB><<<(unsigned)ceil_div(m, RB), 256, sm, s>>>(X, ld, m, n, np, planes, rexp);
   count_launch();
   return cudaGetLastError();
 }
@@ -697,19 +831,12 @@ cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int 
 cudaError_t ozaki_slice_rows(const double* X, int64_t ld, int64_t m, int n, int S, unsigned short* planes, int* rexp,
                              cudaStream_t s) {
   const OzGeom g = ozaki_geometry(m, n);
-  const size_t sm = (size_t)n * SR_ROWS * sizeof(double);
-  cudaError_t e;
-  if (S == 7) {
-    e = cudaFuncSetAttribute(k_slice_rows<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_slice_rows<7><<<(unsigned)ceil_div(m, SR_ROWS), 256, sm, s>>>(X, ld, m, n, g.np, planes, rexp);
-  } else {
-    e = cudaFuncSetAttribute(k_slice_rows<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_slice_rows<6><<<(unsigned)ceil_div(m, SR_ROWS), 256, sm, s>>>(X, ld, m, n, g.np, planes, rexp);
-  }
-  count_launch();
-  return cudaGetLastError();
+  // 32 rows per CTA while the staged tile fits (n <= 512), else 16
+  if (n <= 512)
+    return S == 7 ? launch_slice_rows<7, 32>(X, ld, m, n, g.np, planes, rexp, s)
+                  : launch_slice_rows<6, 32>(X, ld, m, n, g.np, planes, rexp, s);
+  return S == 7 ? launch_slice_rows<7, 16>(X, ld, m, n, g.np, planes, rexp, s)
+                : launch_slice_rows<6, 16>(X, ld, m, n, g.np, planes, rexp, s);
 }
 
 cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, unsigned short* planes,
@@ -722,9 +849,10 @@ cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool fr
   return cudaGetLastError();
 }
 
-cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial, double* W,
-                       int64_t ldw, DevStatus* st, cudaStream_t s) {
+cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
+                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s) {
   const OzGeom g = ozaki_geometry(m, n);
+  if (g.nsplit > max_splits) return cudaErrorInvalidValue;
   OzParams p{};
   p.m = m;
   p.n = n;
@@ -735,10 +863,13 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
   p.out = partial;
   p.ldo = n;
   p.st = st;
-  dim3 grid((unsigned)g.ntiles, (unsigned)g.nsplit);
+  p.ntiles = g.ntiles;
+  p.nitems = (int64_t)g.ntiles * g.nsplit;
+  dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.col_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.col_b;
-  cudaError_t e = S == 7 ? launch_oz<7, OZ_GRAM>(a, b, p, grid, s) : launch_oz<6, OZ_GRAM>(a, b, p, grid, s);
+  cudaError_t e = S == 7 ? launch_oz<7, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI>(a, b, p, grid, s)
+                         : launch_oz<6, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI>(a, b, p, grid, s);
   if (e != cudaSuccess) return e;
   dim3 rg((unsigned)ceil_div(n, 128), (unsigned)n);
   k_oz_gram_reduce<<<rg, 128, 0, s>>>(partial, g.nsplit, n, W, ldw);
@@ -757,11 +888,14 @@ cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* 
   p.out = Q;
   p.ldo = ldq;
   p.st = st;
-  p.ntile_j = g.ntile_j;
-  dim3 grid((unsigned)(g.ntile_j * ceil_div(m, OZ_BM)));
+  p.ntile_j = (int)ceil_div(n, OZ_QFORM_BN);
+  p.ntiles = 1;
+  p.nitems = (int64_t)p.ntile_j * ceil_div(m, OZ_BM);
+  dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.row_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.rinv_b;
-  return S == 7 ? launch_oz<7, OZ_QFORM>(a, b, p, grid, s) : launch_oz<6, OZ_QFORM>(a, b, p, grid, s);
+  return S == 7 ? launch_oz<7, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI>(a, b, p, grid, s)
+                : launch_oz<6, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI>(a, b, p, grid, s);
 }
 
 }  // namespace cqr2

@@ -1,0 +1,89 @@
+"""Host check of the split-precision accumulator -> FP64 conversion.
+
+The kernel turns the two int64 fixed-point accumulators (hi 2^32 + lo) 2^E
+into a double with integer operations. The same routine, compiled for the
+host, is compared with exact rational arithmetic (Python's int -> float and
+Fraction -> float round to nearest, ties to even) on random, tie, carry,
+sign and subnormal cases.
+"""
+from __future__ import annotations
+
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1710_08471_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def conv(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("conv") / "fixed_conv_check")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "native", "fixed_conv_check.cpp"),
+                    "-o", exe], check=True)
+
+    def run(cases):
+        inp = "".join(f"{h} {l} {e}\n" for h, l, e in cases)
+        out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
+        return [struct.unpack("<d", int(w, 16).to_bytes(8, "little"))[0] for w in out]
+
+    return run
+
+
+def exact(h, l, e):
+    v = Fraction(h * (1 << 32) + l) * (Fraction(2) ** e)
+    try:
+        return float(v)
+    except OverflowError:
+        return float("inf") if v > 0 else float("-inf")
+
+
+def _check(conv, cases):
+    got = conv(cases)
+    for (h, l, e), g in zip(cases, got):
+        want = exact(h, l, e)
+        assert struct.pack("<d", g) == struct.pack("<d", want), (h, l, e, g, want)
+
+
+def test_random(conv):
+    rng = random.Random(7)
+    cases = []
+    for _ in range(20000):
+        bh, bl = rng.randint(0, 61), rng.randint(0, 61)
+        h = rng.randint(-(1 << bh), 1 << bh)
+        l = rng.randint(-(1 << bl), 1 << bl)
+        cases.append((h, l, rng.randint(-120, 40)))
+    _check(conv, cases)
+
+
+def test_ties_carries_and_signs(conv):
+    cases = []
+    for k in range(0, 40):
+        # exactly half an ulp above a representable value (ties to even both ways)
+        for m in ((1 << 53) - 1, (1 << 53) - 2, (1 << 52) + 1, (1 << 52)):
+            t = (2 * m + 1) << k
+            for sgn in (1, -1):
+                v = sgn * t
+                cases.append((v >> 32, v - ((v >> 32) << 32), -10))
+                cases.append(((v >> 32) - 1, v - ((v >> 32) << 32) + (1 << 32), 3))
+    # rounding carry into the exponent, zero, hi/lo cancellation, lo < 0
+    cases += [(0, 0, 0), (1, -(1 << 32), 5), (0, (1 << 54) - 1, 0), ((1 << 21) - 1, (1 << 32) - 1, 0),
+              (-(1 << 40), 123, -7), (5, -(1 << 61), 2), (-(1 << 61), -(1 << 61), -200)]
+    _check(conv, cases)
+
+
+def test_subnormal_and_overflow(conv):
+    rng = random.Random(3)
+    cases = [(rng.randint(-(1 << 40), 1 << 40), rng.randint(-(1 << 50), 1 << 50), rng.randint(-1200, -1050))
+             for _ in range(3000)]
+    cases += [(1, 0, -1106), (0, 1, -1074), (0, 1, -1075), (0, 3, -1076), (0, 2, -1076), ((1 << 40), 0, 980),
+              (-(1 << 40), 0, 990)]
+    _check(conv, cases)

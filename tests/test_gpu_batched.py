@@ -46,6 +46,21 @@ def test_factor_rows_uneven_m(cq, prec, scale):
             check(A, to_host(Q), to_host(R), kappa, scale)
 
 
+@pytest.mark.parametrize("prec,scale", [(0, 1.0), (1, 10.0)])
+@pytest.mark.parametrize("n", [16, 64])
+def test_factor_rows_more_ranges_than_full_size(cq, prec, scale, n):
+    # Row counts just above a multiple of the CTA target round to shorter (and
+    # so more) Gram row ranges than the plan's full size does; the partial
+    # buffers must hold them (n = 16: 38900 rows make 304 ranges against 293
+    # at 2^18 rows on the split-precision path).
+    with cq.Plan(1 << 18, n, precision=prec) as p:
+        for m in (38900, 38913, 77801, 155000, 155701, (1 << 18) - 1):
+            A = synth.make_matrix(m, n, 1e3, seed=m)
+            Q, R, info = p.factor_rows(to_dev(A))
+            assert info.status == 0
+            check(A, to_host(Q), to_host(R), 1e3, scale)
+
+
 def test_lstsq_rows(cq):
     n = 32
     with cq.Plan(5000, n) as p:
