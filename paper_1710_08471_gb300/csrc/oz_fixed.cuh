@@ -84,4 +84,35 @@ OZ_HD double oz_fixed_to_double(long long hi, long long lo, int E) {
   return oz_bits_to_double(bits | (neg ? 1ull << 63 : 0ull));
 }
 
+// The accumulators as kept by the kernel: T = X 2^24 + Y with X holding
+// groups 0-3 and Y groups 4-6. Exact conversion through (hi, lo).
+OZ_HD double oz_xy_to_double(long long X, long long Y, int E) {
+  const long long hi = X >> 8;  // T = hi 2^32 + ((X mod 2^8) 2^24 + Y)
+  const long long lo = (long long)((unsigned long long)(X & 0xFF) << 24) + Y;
+  return oz_fixed_to_double(hi, lo, E);
+}
+
+// Faster conversion of T = X 2^24 + Y (|X| < 2^61, |Y| < 2^55) to within one
+// ulp of T 2^E: scale T by 2^-sh so that it fits 62 bits (the bits of Y that
+// fall off are below 2^-61 of it), then round that int64 to nearest.
+OZ_HD double oz_xy_to_double_fast(long long X, long long Y, int E) {
+  const unsigned long long ax = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
+  const int bl = 64 - oz_clz64(ax);  // bit length of |X|
+  const int sh = bl > 38 ? bl - 38 : 0;
+  const long long Z = (long long)((unsigned long long)X << (24 - sh)) + (Y >> sh);
+  const bool neg = Z < 0;
+  unsigned long long u = neg ? 0ull - (unsigned long long)Z : (unsigned long long)Z;
+  if (u == 0) return 0.0;
+  const int lz = oz_clz64(u);
+  u <<= lz;
+  unsigned long long mant = u >> 11;
+  const unsigned long long rb = (u >> 10) & 1ull, st = (u & 0x3FFull) != 0 ? 1ull : 0ull;
+  const int biased = 63 - lz + E + sh + 1023;
+  if (biased < 1) return oz_xy_to_double(X, Y, E);  // subnormal: rare, exact path
+  mant += rb & (st | (mant & 1ull));
+  unsigned long long bits = ((unsigned long long)(biased - 1) << 52) + mant;
+  if (biased > 2046) bits = 0x7FF0000000000000ull;
+  return oz_bits_to_double(bits | (neg ? 1ull << 63 : 0ull));
+}
+
 }  // namespace cqr2

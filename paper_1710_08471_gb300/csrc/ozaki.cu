@@ -18,9 +18,10 @@
 // A chunk of 128 contraction indices keeps every group sum an integer below
 // 2^24, so the FP32 accumulation is exact. After each chunk the epilogue
 // warps move the group sums into two int64 fixed-point accumulators per
-// output (groups 0-2 and 3-6), which stays exact as well. The only rounding
-// is the one of x' and the final conversion to FP64, done with integer
-// operations.
+// output (T = X 2^24 + Y, X: groups 0-3, Y: groups 4-6), which stays exact
+// as well. The only roundings are the one of x' and the final conversion to
+// FP64 with integer operations: correctly rounded for the Gram, within one
+// ulp for the Q-form (a shorter sequence; far below its truncation error).
 //
 // Kernel: persistent, one CTA per SM, 128 x 32 output tiles, BF16 operands
 // K-major in 128-byte swizzled shared memory, loaded by TMA (3-D maps over
@@ -338,12 +339,15 @@ enum { OZ_GRAM = 0, OZ_QFORM = 1 };
 // Tile shapes. The Gram uses 128 x 64 tiles (more operand reuse; the S group
 // accumulators take 64 S <= 448 TMEM columns, one buffer). The Q-form uses
 // 128 x 32 tiles with two accumulator buffers (2 x 32 S <= 448 columns) and
-// 16 epilogue warps, since its epilogue (one conversion per output) is as
-// long as its MMAs.
-constexpr int OZ_GRAM_BN = 64, OZ_GRAM_EPI = 8;
-constexpr int OZ_QFORM_BN = 32, OZ_QFORM_EPI = 16;
+// 16 epilogue warps, since its epilogue (S conversions to integer and one to
+// FP64 per output) is as long as its MMAs. The epilogue warps may also be
+// split into two groups that take alternate tiles (NGRP = 2); measured on
+// 2^20 x 128 that was slower (1.88 ms against 1.37 ms per Q-form), so both
+// shapes run one group.
+constexpr int OZ_GRAM_BN = 64, OZ_GRAM_EPI = 8, OZ_GRAM_GRP = 1;
+constexpr int OZ_QFORM_BN = 32, OZ_QFORM_EPI = 16, OZ_QFORM_GRP = 1;
 
-template <int S, int BN, int EPI>
+template <int S, int BN, int EPI, int NGRP>
 struct OzCfg {
   static constexpr int NBUF = 2 * S * BN <= 512 ? 2 : 1;         // accumulator buffers in TMEM
   static constexpr int THREADS = 64 + 32 * EPI;                   // producer, MMA, epilogue warps
@@ -352,13 +356,14 @@ struct OzCfg {
   static constexpr int NA = (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES < 8
                                 ? (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES
                                 : 8;                              // A ring slots
-  static constexpr int CPT = BN / (EPI / 4);                      // columns per epilogue thread
+  static constexpr int CPT = BN * 4 * NGRP / EPI;                 // columns per epilogue thread
   static constexpr int TMAX = 256 / BN;                           // products per MMA (N <= 256)
   static constexpr int NBAR = 2 * NA + 4 + 2 * NBUF * S;
   static constexpr size_t SMEM = 1024 + (size_t)NA * A_BYTES + (size_t)2 * S * B_BYTES + 8 * NBAR + 16;
   static_assert(NBUF * S * BN <= 512, "accumulators must fit in TMEM");
   static_assert(CPT == 8 || CPT == 16 || CPT == 32, "epilogue load width");
   static_assert(NA >= S, "a K-block of A slices must fit the ring");
+  static_assert((EPI / NGRP) % 4 == 0 && (NGRP == 1 || NBUF == 2), "epilogue groups");
 };
 
 struct OzParams {
@@ -446,16 +451,16 @@ __device__ __forceinline__ void mad_wide(long long& acc, int x, int w) {
 }
 
 // Adds the group sums of one chunk (exact integers in FP32) into the two
-// fixed-point accumulators: groups 0-2 into hi with weights 2^16, 2^8, 1,
-// groups 3-6 into lo with weights 2^24 .. 1.
+// fixed-point accumulators, T = X 2^24 + Y: groups 0-3 into X with weights
+// 2^24, 2^16, 2^8, 1 and groups 4-6 into Y with weights 2^16, 2^8, 1.
 template <int G, int N>
-__device__ __forceinline__ void oz_accumulate(const uint32_t* v, long long* hi, long long* lo) {
-  constexpr int W = G <= 2 ? 1 << (8 * (2 - G)) : 1 << (8 * (6 - G));
+__device__ __forceinline__ void oz_accumulate(const uint32_t* v, long long* X, long long* Y) {
+  constexpr int W = G <= 3 ? 1 << (8 * (3 - G)) : 1 << (8 * (6 - G));
 #pragma unroll
   for (int cc = 0; cc < N; ++cc) {
     const int x = __float2int_rn(__uint_as_float(v[cc]));
-    if (G <= 2) mad_wide(hi[cc], x, W);
-    else mad_wide(lo[cc], x, W);
+    if (G <= 3) mad_wide(X[cc], x, W);
+    else mad_wide(Y[cc], x, W);
   }
 }
 
@@ -476,13 +481,13 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
 
 // Drains group G of one chunk for this thread's CPT columns (16 at a time).
 template <int G, int CPT>
-__device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* hi, long long* lo) {
-  constexpr int W = CPT < 16 ? CPT : 16;
+__device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* X, long long* Y) {
+  constexpr int W = CPT >= 32 ? 16 : 8;  // columns per TMEM load (register budget)
 #pragma unroll
   for (int h = 0; h < CPT / W; ++h) {
     uint32_t v[W];
     tmem_ld<W>(ta + W * h, v);
-    oz_accumulate<G, W>(v, hi + W * h, lo + W * h);
+    oz_accumulate<G, W>(v, X + W * h, Y + W * h);
   }
 }
 
@@ -493,10 +498,10 @@ __device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* hi, long 
 // epilogue drains a group as soon as its last product is done and the MMAs
 // overwrite it only after that drain. Warp w of the epilogue reads TMEM lanes
 // 32 (w % 4) .. +31 (its rows) and one column slice of each group.
-template <int S, int MODE, int BN, int EPI>
-__global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
+template <int S, int MODE, int BN, int EPI, int NGRP>
+__global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzParams p) {
-  using C = OzCfg<S, BN, EPI>;
+  using C = OzCfg<S, BN, EPI, NGRP>;
   constexpr int NA = C::NA, NBUF = C::NBUF, CPT = C::CPT;
   constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
   constexpr uint32_t ACC_COLS = S * BN;  // one accumulator buffer
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
     }
     for (int i = 0; i < NBUF * S; ++i) {
       mbar_init(&accfull[i], 1);
-      mbar_init(&accempty[i], EPI);
+      mbar_init(&accempty[i], EPI / NGRP);  // one group drains a chunk
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -542,26 +547,40 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
   const int64_t it_begin = oz_range_begin<MODE, BN>(p, blockIdx.x, gridDim.x);
   const int64_t it_end = oz_range_begin<MODE, BN>(p, blockIdx.x + 1, gridDim.x);
 
+  // Ring positions run on across items: A slot and its phase parity, B buffer
+  // and its parity. The single issuing threads keep their loops short (no
+  // divisions, slices and products unrolled): an MMA of N < 192 costs about
+  // as long to issue as to run.
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
-      int64_t gk = 0, q = 0;  // running K-block and A-slice counters
+      int slot = 0, buf = 0;
+      uint32_t aph = 0, bph = 0;
+      bool awrapped = false, bwrapped = false;  // ring slots used once already
       for (int64_t it = it_begin; it < it_end && ok; ++it) {
         const OzItem w = oz_item<MODE, BN>(p, it);
-        for (int kb = 0; kb < w.nk && ok; ++kb, ++gk) {
-          const int buf = (int)(gk & 1);
+        for (int kb = 0; kb < w.nk; ++kb) {
           const int k0 = (int)(w.kbase + (int64_t)kb * OZ_BK);
-          if (gk >= 2) ok = mbar_wait(&bempty[buf], (uint32_t)(((gk >> 1) - 1) & 1), p.st);
-          if (!ok) break;
+          if (bwrapped && !(ok = mbar_wait(&bempty[buf], bph ^ 1u, p.st))) break;
           mbar_expect_tx(&bfull[buf], S * B_BYTES);
+#pragma unroll
           for (int t = 0; t < S; ++t)
             tma_load_3d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], k0, (int)w.j0, t);
-          for (int s = 0; s < S; ++s, ++q) {
-            const int slot = (int)(q % NA);
-            if (q >= NA) ok = mbar_wait(&aempty[slot], (uint32_t)(((q / NA) - 1) & 1), p.st);
-            if (!ok) break;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            if (awrapped && !(ok = mbar_wait(&aempty[slot], aph ^ 1u, p.st))) break;
             mbar_expect_tx(&afull[slot], A_BYTES);
             tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)w.i0, s);
+            if (++slot == NA) {
+              slot = 0;
+              aph ^= 1u;
+              awrapped = true;
+            }
+          }
+          if (!ok) break;
+          if ((buf ^= 1) == 0) {
+            bph ^= 1u;
+            bwrapped = true;
           }
         }
       }
@@ -572,75 +591,100 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
       // kind::f16, BF16 A and B, FP32 accumulate, both K-major, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
       bool ok = true;
-      int64_t gk = 0, q = 0, gc = 0;  // running K-block, A-slice and chunk counters
+      int slot = 0, buf = 0;
+      uint32_t aph = 0, bph = 0;
+      int64_t gc = 0;            // chunks issued
+      int64_t used0 = 0, used1 = 0;  // two epilogue groups: chunks issued into buffer 0, 1
       for (int64_t it = it_begin; it < it_end && ok; ++it) {
         const OzItem w = oz_item<MODE, BN>(p, it);
-        for (int kb = 0; kb < w.nk && ok; ++kb, ++gk) {
-          const int buf = (int)(gk & 1);
-          const bool first = (kb & 1) == 0;
+        const int par_it = (int)((it - it_begin) & 1);
+        for (int kb = 0; kb < w.nk; ++kb) {
+          const bool first = (kb & 1) == 0;  // the chunk's first K-block overwrites its groups
           const bool last = (kb & 1) == 1 || kb == w.nk - 1;
-          const int ab = (int)(gc % NBUF);   // accumulator buffer of this chunk
-          const int64_t use = gc / NBUF;     // earlier chunks in this buffer
+          // Accumulator buffer of this chunk. One epilogue group: chunks
+          // alternate between the buffers. Two groups: group g drains the
+          // items of parity g from buffer g only, so that each waits on its
+          // buffer's phases strictly in turn (a waiter two phases ahead
+          // would see the earlier phase's parity as complete).
+          const int ab = NGRP == 2 ? par_it : (NBUF == 2 ? (int)(gc & 1) : 0);
+          const int64_t use = NGRP == 2 ? (par_it ? used1 : used0) : (NBUF == 2 ? gc >> 1 : gc);  // earlier chunks in it
+          const bool wait_acc = first && use >= 1;
           const uint32_t acc = tmem + (uint32_t)ab * ACC_COLS;
-          ok = mbar_wait(&bfull[buf], (uint32_t)((gk >> 1) & 1), p.st);
-          if (!ok) break;
-          for (int s = 0; s < S && ok; ++s, ++q) {
-            const int slot = (int)(q % NA);
-            ok = mbar_wait(&afull[slot], (uint32_t)((q / NA) & 1), p.st);
-            if (!ok) break;
+          if (!(ok = mbar_wait(&bfull[buf], bph, p.st))) break;
+          const uint64_t db0 = sdesc(sB + buf * S * B_BYTES);
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            if (!(ok = mbar_wait(&afull[slot], aph, p.st))) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t da = sdesc(sA + slot * A_BYTES);
             // Products (s, t), t = t0 .. t0+nt-1, in one MMA of N = BN nt: the
             // B slices lie back to back in shared memory (one 1024-byte pitch
             // per 8 rows throughout) and group g = s + t is the BN-column
             // accumulator at column BN g, so each product lands in its group.
-            for (int t0 = 0; t0 + s < S && ok; t0 += C::TMAX) {
-              const int nt = min(C::TMAX, S - s - t0);
-              if (first && s == 0 && use >= 1) {  // the first write of groups t0.. in this buffer
-                for (int g = t0; g < t0 + nt && ok; ++g)
-                  ok = mbar_wait(&accempty[ab * S + g], (uint32_t)((use - 1) & 1), p.st);
+#pragma unroll
+            for (int t0 = 0; t0 < S - s; t0 += C::TMAX) {
+              const int nt = S - s - t0 < C::TMAX ? S - s - t0 : C::TMAX;
+              if (s == 0 && wait_acc) {  // first write of groups t0 .. t0+nt-1 in this buffer
+#pragma unroll
+                for (int g = t0; g < t0 + nt; ++g)
+                  if (!(ok = mbar_wait(&accempty[ab * S + g], (uint32_t)((use - 1) & 1), p.st))) break;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
               }
               const uint32_t idesc_n = idesc | ((uint32_t)((BN * nt) >> 3) << 17);
-              const uint64_t db = sdesc(sB + (buf * S + t0) * B_BYTES);
+              const uint64_t db = db0 + (uint64_t)((t0 * B_BYTES) >> 4);
+              const uint32_t d = acc + (uint32_t)((s + t0) * BN);
+              mma_bf16(d, da, db, idesc_n, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
-              for (int k = 0; k < OZ_BK / 16; ++k)
-                mma_bf16(acc + (uint32_t)((s + t0) * BN), da + 2 * k, db + 2 * k, idesc_n,
-                         (first && s == 0 && k == 0) ? 0u : 1u);
+              for (int k = 1; k < OZ_BK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc_n, 1u);
             }
             if (!ok) break;
             mma_commit(&aempty[slot]);
             if (last) mma_commit(&accfull[ab * S + s]);  // every product of group s is issued
+            if (++slot == NA) {
+              slot = 0;
+              aph ^= 1u;
+            }
           }
           if (!ok) break;
           mma_commit(&bempty[buf]);
-          if (last) ++gc;
+          if ((buf ^= 1) == 0) bph ^= 1u;
+          if (last) {
+            ++gc;
+            if (NGRP == 2) (par_it ? used1 : used0) += 1;
+          }
         }
       }
       if (!ok) report_timeout(p.st);
     }
   } else {
-    const int q4 = warp & 3;
-    const int cs = (warp - 2) >> 2;  // column slice of each group
+    const int ew = warp - 2;                            // epilogue warp
+    const int grp = NGRP == 2 ? ew / (EPI / NGRP) : 0;  // its group: items of its parity
+    const int q4 = warp & 3;                            // TMEM lane quarter (rows)
+    const int cs = (ew % (EPI / NGRP)) >> 2;            // column slice of each accumulator
     bool ok = true;
-    int64_t gc = 0;
+    int64_t gc = 0;  // chunks drained (by this group)
     for (int64_t it = it_begin; it < it_end && ok; ++it) {
+      if (NGRP == 2 && (int)((it - it_begin) & 1) != grp) continue;
       const OzItem w = oz_item<MODE, BN>(p, it);
-      long long hi[CPT], lo[CPT];
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) hi[c] = lo[c] = 0;
       const int nchunks = (w.nk + 1) >> 1;
+      long long X[CPT], Y[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) X[c] = Y[c] = 0;
+      const int64_t row = w.i0 + q4 * 32 + lane;
+      const int64_t nrow = MODE == OZ_GRAM ? p.n : p.m;
+      // Q-form items are short: load the row exponent now, off the conversion's path
+      const int ea = MODE == OZ_QFORM && row < nrow ? p.eA[row] : 0;
       for (int c = 0; c < nchunks && ok; ++c, ++gc) {
-        const int ab = (int)(gc % NBUF);
-        const uint32_t par = (uint32_t)((gc / NBUF) & 1);
+        const int ab = NGRP == 2 ? grp : (int)(gc % NBUF);
+        const uint32_t par = (uint32_t)((NGRP == 2 ? gc : gc / NBUF) & 1);
         const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)ab * ACC_COLS + (uint32_t)(cs * CPT);
 #define OZ_DRAIN(G)                                                        \
   if (G < S && ok) {                                                       \
     ok = mbar_wait(&accfull[ab * S + G], par, p.st);                       \
     if (ok) {                                                              \
       asm volatile("tcgen05.fence::after_thread_sync;");                   \
-      oz_drain_group<G, CPT>(ta + G * BN, hi, lo);                         \
+      oz_drain_group<G, CPT>(ta + G * BN, X, Y);                           \
       asm volatile("tcgen05.fence::before_thread_sync;");                  \
       __syncwarp();                                                        \
       if (lane == 0) mbar_arrive(&accempty[ab * S + G]);                   \
@@ -656,20 +700,21 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI>::THREADS, 1)
 #undef OZ_DRAIN
       }
       if (!ok) break;
-      const int64_t row = w.i0 + q4 * 32 + lane;
-      const int64_t nrow = MODE == OZ_GRAM ? p.n : p.m;
       if (row < nrow) {
-        const int ea = p.eA[row];
+        const int ea2 = MODE == OZ_GRAM ? p.eA[row] : ea;
         double* out = MODE == OZ_GRAM ? p.out + (int64_t)w.split * p.n * p.n : p.out;
         const int64_t ld = MODE == OZ_GRAM ? p.n : p.ldo;
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
           const int64_t col = w.j0 + cs * CPT + cc;
           if (col < p.n) {
-            const int eb = p.eB[col];
-            out[row + col * ld] = (ea >= EXP_NONFINITE || eb >= EXP_NONFINITE)
+            const int e2 = p.eB[col];
+            // Gram: exact rounding; Q-form: within one ulp (far below its
+            // truncation error), with a shorter integer sequence
+            out[row + col * ld] = (ea2 >= EXP_NONFINITE || e2 >= EXP_NONFINITE)
                                       ? __longlong_as_double(0x7FF8000000000000ll)
-                                      : oz_fixed_to_double(hi[cc], lo[cc], ea + eb - 14 - 48);
+                                  : MODE == OZ_GRAM ? oz_xy_to_double(X[cc], Y[cc], ea2 + e2 - 14 - 48)
+                                                    : oz_xy_to_double_fast(X[cc], Y[cc], ea2 + e2 - 14 - 48);
           }
         }
       }
@@ -713,11 +758,11 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int S, int MODE, int BN, int EPI>
+template <int S, int MODE, int BN, int EPI, int NGRP>
 cudaError_t launch_oz(const CUtensorMap& a, const CUtensorMap& b, const OzParams& p, dim3 grid, cudaStream_t s) {
-  using Cfg = OzCfg<S, BN, EPI>;
+  using Cfg = OzCfg<S, BN, EPI, NGRP>;
   static_assert(Cfg::SMEM <= 227 * 1024, "shared memory per CTA");
-  auto kern = k_ozaki_gemm<S, MODE, BN, EPI>;
+  auto kern = k_ozaki_gemm<S, MODE, BN, EPI, NGRP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
   kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, b, p);
@@ -868,8 +913,8 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
   dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.col_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.col_b;
-  cudaError_t e = S == 7 ? launch_oz<7, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI>(a, b, p, grid, s)
-                         : launch_oz<6, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI>(a, b, p, grid, s);
+  cudaError_t e = S == 7 ? launch_oz<7, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI, OZ_GRAM_GRP>(a, b, p, grid, s)
+                         : launch_oz<6, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI, OZ_GRAM_GRP>(a, b, p, grid, s);
   if (e != cudaSuccess) return e;
   dim3 rg((unsigned)ceil_div(n, 128), (unsigned)n);
   k_oz_gram_reduce<<<rg, 128, 0, s>>>(partial, g.nsplit, n, W, ldw);
@@ -894,8 +939,8 @@ cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* 
   dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.row_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.rinv_b;
-  return S == 7 ? launch_oz<7, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI>(a, b, p, grid, s)
-                : launch_oz<6, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI>(a, b, p, grid, s);
+  return S == 7 ? launch_oz<7, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s)
+                : launch_oz<6, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s);
 }
 
 }  // namespace cqr2

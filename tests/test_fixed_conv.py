@@ -1,10 +1,10 @@
 """Host check of the split-precision accumulator -> FP64 conversion.
 
-The kernel turns the two int64 fixed-point accumulators (hi 2^32 + lo) 2^E
-into a double with integer operations. The same routine, compiled for the
-host, is compared with exact rational arithmetic (Python's int -> float and
-Fraction -> float round to nearest, ties to even) on random, tie, carry,
-sign and subnormal cases.
+The kernel turns its two int64 fixed-point accumulators into a double with
+integer operations: exactly (hi 2^32 + lo, or X 2^24 + Y) for the Gram, and
+to within one ulp for the Q-form. The same routines, compiled for the host,
+are compared with exact rational arithmetic (Python's Fraction -> float rounds
+to nearest, ties to even) on random, tie, carry, sign and subnormal cases.
 """
 from __future__ import annotations
 
@@ -30,16 +30,16 @@ def conv(tmp_path_factory):
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "native", "fixed_conv_check.cpp"),
                     "-o", exe], check=True)
 
-    def run(cases):
-        inp = "".join(f"{h} {l} {e}\n" for h, l, e in cases)
+    def run(cases, mode=0):
+        inp = "".join(f"{mode} {h} {l} {e}\n" for h, l, e in cases)
         out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split()
         return [struct.unpack("<d", int(w, 16).to_bytes(8, "little"))[0] for w in out]
 
     return run
 
 
-def exact(h, l, e):
-    v = Fraction(h * (1 << 32) + l) * (Fraction(2) ** e)
+def exact(h, l, e, shift=32):
+    v = Fraction(h * (1 << shift) + l) * (Fraction(2) ** e)
     try:
         return float(v)
     except OverflowError:
@@ -87,3 +87,38 @@ def test_subnormal_and_overflow(conv):
     cases += [(1, 0, -1106), (0, 1, -1074), (0, 1, -1075), (0, 3, -1076), (0, 2, -1076), ((1 << 40), 0, 980),
               (-(1 << 40), 0, 990)]
     _check(conv, cases)
+
+
+def _ulp(x):
+    import math
+
+    return math.ulp(x)
+
+
+def test_xy_exact(conv):
+    rng = random.Random(11)
+    cases = [(rng.randint(-(1 << 60), 1 << 60) >> rng.randint(0, 60), rng.randint(-(1 << 54), 1 << 54) >> rng.randint(0, 54),
+              rng.randint(-150, 30)) for _ in range(20000)]
+    cases += [(0, 0, 0), (-1, (1 << 24) - 1, 0), (1, -(1 << 24), 3), (-(1 << 60), -(1 << 54), -100), (255, -1, -1080)]
+    got = conv(cases, 1)
+    for (x, y, e), g in zip(cases, got):
+        want = exact(x, y, e, 24)
+        assert struct.pack("<d", g) == struct.pack("<d", want), (x, y, e, g, want)
+
+
+def test_xy_fast_within_one_ulp(conv):
+    rng = random.Random(12)
+    cases = [(rng.randint(-(1 << 60), 1 << 60) >> rng.randint(0, 60), rng.randint(-(1 << 54), 1 << 54) >> rng.randint(0, 54),
+             rng.randint(-150, 30)) for _ in range(30000)]
+    # X alone near the shift threshold, Y cancelling X, zero
+    for b in range(30, 45):
+        cases += [((1 << b) - 1, -(1 << 53), -60), (-(1 << b), (1 << 54) - 1, -60), (1 << b, -(1 << (b + 24)) // (1 << 24), 0)]
+    cases += [(0, 0, 0), (0, 5, -3), (-7, 0, 2), (1, -(1 << 24), 0)]
+    got = conv(cases, 2)
+    for (x, y, e), g in zip(cases, got):
+        t = x * (1 << 24) + y
+        want = exact(x, y, e, 24)
+        if abs(x) < (1 << 38):  # no bits dropped: correctly rounded
+            assert struct.pack("<d", g) == struct.pack("<d", want), (x, y, e, g, want)
+        else:
+            assert abs(Fraction(g) - Fraction(t) * Fraction(2) ** e) <= Fraction(_ulp(want)), (x, y, e, g, want)
