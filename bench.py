@@ -314,7 +314,9 @@ def bench_ours(args, ws, rank, local):
         ms = e0.elapsed_time(e1) / steps
         st = pl.stage_times() if profile else None
         pl.set_profiling(False)
-        return ms, launches, {k: v[0] / v[1] for k, v in st.items() if v[1] > 0} if st else {}
+        # per step: a stage that runs several times in one factorization (the
+        # split-precision slicing) is summed over its occurrences
+        return ms, launches, {k: v[0] / steps for k, v in st.items() if v[1] > 0} if st else {}
 
     def roofline_of(per_stage, precision, fz, clk):
         work = stage_work(m, n, precision, fz)
