@@ -53,6 +53,20 @@ struct cqr2_plan_st {
   double* hA_dev = nullptr;
   double* hQ_dev = nullptr;
   double* hR_dev = nullptr;
+  // cqr2_factor_host overlaps its copies with the factorization: A arrives
+  // in row blocks on a copy stream while the pass-1 Gram consumes them, and
+  // Q leaves block by block as the last Q-form writes it.
+  cudaStream_t copy_stream = nullptr;
+  double* hx_partial = nullptr;  // Gram partials of the row blocks (HX_BLOCKS x hx_cap ranges)
+  int64_t hx_cap = 0;
+  std::vector<cudaEvent_t> hx_ev;  // [0, HX_BLOCKS): A block in; [HX_BLOCKS, 2 HX_BLOCKS): Q block out; 2 more
+  struct {
+    bool on = false;         // a host-buffer call is in progress
+    bool a_pending = false;  // A's blocks are still in flight (no kernel has waited for them)
+    bool q_sent = false;     // Q has been copied out block by block
+    double* hQ = nullptr;
+    int64_t ldq = 0;
+  } hx;
   // split-precision (Ozaki) path
   int oz_S = 0;  // slices per entry, 0 = native FP64
   unsigned short* oz_planes = nullptr;
@@ -116,25 +130,39 @@ cudaEvent_t take_event(cqr2_plan_st* p) {
   return p->ev_pool[p->ev_used++];
 }
 
-// Records CUDA events on the plan's stream around one stage when profiling.
+// Records CUDA events around one stage when profiling, on the plan's stream
+// or on another one (the host-copy stream).
 struct Stage {
   cqr2_plan_st* p;
   int id;
+  cudaStream_t s;
   cudaEvent_t a = nullptr;
-  Stage(cqr2_plan_st* p_, int id_) : p(p_), id(id_) {
+  Stage(cqr2_plan_st* p_, int id_, cudaStream_t s_ = nullptr) : p(p_), id(id_), s(s_ ? s_ : p_->stream) {
     if (p->profiling && p->ev_marks.size() < MAX_MARKS) {
       a = take_event(p);
-      if (a) cudaEventRecord(a, p->stream);
+      if (a) cudaEventRecord(a, s);
     }
   }
   ~Stage() {
     if (!a) return;
     cudaEvent_t b = take_event(p);
     if (!b) return;
-    cudaEventRecord(b, p->stream);
+    cudaEventRecord(b, s);
     p->ev_marks.push_back({id, {a, b}});
   }
 };
+
+// ---- host-buffer calls: row blocks of the copies
+constexpr int HX_BLOCKS = 8;
+inline int64_t hx_row(int64_t m, int r) { return r == HX_BLOCKS ? m : ((m * r / HX_BLOCKS) & ~(int64_t)63); }
+
+// A kernel about to read A (the host-staged input) as a whole waits for all
+// of its blocks first; the blocked pass-1 Gram waits block by block instead.
+cudaError_t hx_wait_input(cqr2_plan_st* p, cudaStream_t s) {
+  if (!p->hx.on || !p->hx.a_pending) return cudaSuccess;
+  p->hx.a_pending = false;
+  return cudaStreamWaitEvent(s, p->hx_ev[HX_BLOCKS - 1], 0);
+}
 
 cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   TRY(cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, p->stream));
@@ -177,6 +205,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
   const int64_t m = p->cm;
   cudaStream_t s = p->stream;
   if (!pass_base) TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  TRY(hx_wait_input(p, s));
   for (int pass = 1; pass <= 2; ++pass) {
     const double* X = pass == 1 ? dA : dQ;
     const int64_t ldx = pass == 1 ? lda : ldq;
@@ -222,8 +251,28 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   // ---- pass 1: W1 = A^T A, [L1, Y1] = CholInv(W1)
   {
     Stage st(p, CQR2_STAGE_GRAM1);
-    TRY(gram_partials(dA, lda, p->cm, n, p->g, p->partial, s));
-    TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+    if (p->hx.on && p->hx.a_pending && pass_base == 0) {
+      // A is arriving in row blocks: each block's row ranges go to their own
+      // partials as soon as the block has landed; one fixed-order sum follows.
+      const int64_t per_split = (int64_t)p->g.ntiles_total * p->g.T * p->g.T;
+      int64_t used = 0;
+      for (int b = 0; b < HX_BLOCKS; ++b) {
+        const int64_t r0 = hx_row(p->cm, b), r1 = hx_row(p->cm, b + 1);
+        TRY(cudaStreamWaitEvent(s, p->hx_ev[b], 0));
+        if (r1 <= r0) continue;
+        const GramGeom gr = gram_geometry(r1 - r0, n, p->hx_cap, p->gram_cps);
+        TRY(gram_partials(dA + r0, lda, r1 - r0, n, gr, p->hx_partial + used * per_split, s));
+        used += gr.nsplit;
+      }
+      p->hx.a_pending = false;
+      GramGeom gall = p->g;
+      gall.nsplit = used;
+      TRY(gram_reduce(p->hx_partial, gall, n, p->W, n, s));
+    } else {
+      TRY(hx_wait_input(p, s));
+      TRY(gram_partials(dA, lda, p->cm, n, p->g, p->partial, s));
+      TRY(gram_reduce(p->partial, p->g, n, p->W, n, s));
+    }
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
@@ -259,12 +308,32 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_QFORM2);
-    if (p->small) {
-      TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
-      TRY(qform_small(dQ, ldq, p->cm, n, p->Rp, dQ, ldq, s));  // in place, panel by panel
-    } else {
-      TRY(gemm_f64(p->cm, n, n, 1.0, X2, ldx2, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    if (p->small) TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
+    // Host-buffer call: the last Q-form runs by row blocks, each copied out on
+    // the copy stream while the next block is formed.
+    const int nb = p->hx.on ? HX_BLOCKS : 1;
+    for (int b = 0; b < nb; ++b) {
+      const int64_t r0 = nb == 1 ? 0 : hx_row(p->cm, b), r1 = nb == 1 ? p->cm : hx_row(p->cm, b + 1);
+      if (r1 > r0) {
+        if (p->small) {
+          TRY(qform_small(dQ + r0, ldq, r1 - r0, n, p->Rp, dQ + r0, ldq, s));  // in place, panel by panel
+        } else {
+          TRY(gemm_f64(r1 - r0, n, n, 1.0, X2 + r0, ldx2, p->Y, n, 0.0, dQ + r0, ldq,
+                       GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+        }
+      }
+      if (p->hx.on) {
+        cudaEvent_t ev = p->hx_ev[HX_BLOCKS + b];
+        TRY(cudaEventRecord(ev, s));
+        TRY(cudaStreamWaitEvent(p->copy_stream, ev, 0));
+        if (r1 > r0) {
+          Stage sd(p, CQR2_STAGE_D2H, p->copy_stream);
+          TRY(cudaMemcpy2DAsync(p->hx.hQ + r0, (size_t)p->hx.ldq * sizeof(double), dQ + r0, (size_t)ldq * sizeof(double),
+                                (size_t)(r1 - r0) * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost, p->copy_stream));
+        }
+      }
     }
+    if (p->hx.on) p->hx.q_sent = true;
   }
   // ---- R = R2 R1 with R2 = L2^T
   {
@@ -285,6 +354,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   const int64_t m = p->cm;
   cudaStream_t s = p->stream;
   TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  TRY(hx_wait_input(p, s));
   {
     Stage st(p, CQR2_STAGE_GRAM1);
     if (p->oz_S) {
@@ -490,6 +560,12 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->copy_stream) {
+    cudaStreamSynchronize(plan->copy_stream);
+    cudaStreamDestroy(plan->copy_stream);
+  }
+  for (cudaEvent_t e : plan->hx_ev) cudaEventDestroy(e);
+  cudaFree(plan->hx_partial);
   cudaFree(plan->hA_dev);
   cudaFree(plan->hQ_dev);
   cudaFree(plan->hR_dev);
@@ -715,25 +791,68 @@ cqr2_status_t cqr2_factor_host(cqr2_plan_t p, const double* hA, int64_t lda, dou
   if ((r = set_rows(p, p->m)) != CQR2_OK) return r;
   const size_t mn = (size_t)p->m * p->n * sizeof(double);
   if (!p->hA_dev) {
+    // Partials for the row-blocked pass-1 Gram: each block may use as many
+    // ranges as the largest CTA target asks for.
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    p->hx_cap = std::max<int64_t>(1, ceil_div((int64_t)GRAM_CPS_MAX * sms, p->g.ntiles_total));
+    const size_t part = (size_t)HX_BLOCKS * p->hx_cap * p->g.ntiles_total * p->g.T * p->g.T * sizeof(double);
     if (cudaMalloc(&p->hA_dev, mn) != cudaSuccess || cudaMalloc(&p->hQ_dev, mn) != cudaSuccess ||
-        cudaMalloc(&p->hR_dev, (size_t)p->n * p->n * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&p->hR_dev, (size_t)p->n * p->n * sizeof(double)) != cudaSuccess ||
+        (!p->oz_S && cudaMalloc(&p->hx_partial, part) != cudaSuccess)) {
       cudaGetLastError();
       cudaFree(p->hA_dev);
       cudaFree(p->hQ_dev);
-      p->hA_dev = p->hQ_dev = nullptr;
+      cudaFree(p->hR_dev);
+      cudaFree(p->hx_partial);
+      p->hA_dev = p->hQ_dev = p->hR_dev = nullptr;
+      p->hx_partial = nullptr;
       return CQR2_ERR_OOM;
     }
   }
-  {
-    Stage st(p, CQR2_STAGE_H2D);
-    TRY(copy_cols(p->hA_dev, p->m, hA, lda, p->m, p->n, cudaMemcpyHostToDevice, p->stream));
+  if (!p->copy_stream) {
+    if (cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return CQR2_ERR_CUDA;
+    p->hx_ev.resize(2 * HX_BLOCKS + 1);
+    for (cudaEvent_t& e : p->hx_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CQR2_ERR_CUDA;
   }
-  if ((r = factor_any(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n)) != CQR2_OK) return r;
+  cudaStream_t cs = p->copy_stream;
+  cudaEvent_t ev_ready = p->hx_ev[2 * HX_BLOCKS];
+  // The copy stream starts after the plan stream's earlier work (the staging
+  // buffers may still be read by a previous call).
+  TRY(cudaEventRecord(ev_ready, p->stream));
+  TRY(cudaStreamWaitEvent(cs, ev_ready, 0));
+  {
+    Stage st(p, CQR2_STAGE_H2D, cs);
+    for (int b = 0; b < HX_BLOCKS; ++b) {
+      const int64_t r0 = hx_row(p->m, b), r1 = hx_row(p->m, b + 1);
+      if (r1 > r0)
+        TRY(cudaMemcpy2DAsync(p->hA_dev + r0, (size_t)p->m * sizeof(double), hA + r0, (size_t)lda * sizeof(double),
+                              (size_t)(r1 - r0) * sizeof(double), (size_t)p->n, cudaMemcpyHostToDevice, cs));
+      TRY(cudaEventRecord(p->hx_ev[b], cs));
+    }
+  }
+  p->hx.on = true;
+  p->hx.a_pending = true;
+  p->hx.q_sent = false;
+  p->hx.hQ = hQ;
+  p->hx.ldq = ldq;
+  r = factor_any(p, p->hA_dev, p->m, p->hQ_dev, p->m, p->hR_dev, p->n);
+  const bool q_sent = p->hx.q_sent;
+  p->hx.on = false;
+  p->hx.a_pending = false;  // every path waits for the input blocks before reading A
+  if (r != CQR2_OK) {
+    cudaStreamSynchronize(cs);
+    return r;
+  }
   {
     Stage st(p, CQR2_STAGE_D2H);
-    TRY(copy_cols(hQ, ldq, p->hQ_dev, p->m, p->m, p->n, cudaMemcpyDeviceToHost, p->stream));
+    if (!q_sent) TRY(copy_cols(hQ, ldq, p->hQ_dev, p->m, p->m, p->n, cudaMemcpyDeviceToHost, p->stream));
     TRY(copy_cols(hR, ldr, p->hR_dev, p->n, p->n, p->n, cudaMemcpyDeviceToHost, p->stream));
   }
+  // the plan stream (and read_info's synchronisation) covers the copy stream
+  TRY(cudaEventRecord(ev_ready, cs));
+  TRY(cudaStreamWaitEvent(p->stream, ev_ready, 0));
   cqr2_info_t local;
   r = read_info(p, info ? info : &local);
   return r;
