@@ -8,6 +8,7 @@ from .cholqr2 import (  # noqa: F401
     PassFailed,
     back_substitution,
     cholinv,
+    cholinv_depth,
     cqr,
     cqr2,
     lstsq,
@@ -16,6 +17,7 @@ from .cholqr2 import (  # noqa: F401
     q_rows,
     rel_error,
     residual,
+    right_solve,
     scqr3,
     shift_of,
     shifted_cqr,

@@ -15,6 +15,10 @@ and notation, with numpy FP64 (IEEE round-to-nearest) arithmetic:
   Q = A R^-1.
 * CQR2    (Algorithm CQR2, Section II-E): (Q1, R1) = CQR(A); (Q, R2) = CQR(Q1);
   R = R2 R1.
+* Inverse depth (Section III-A's triangular inverted blocks, the InverseDepth
+  parameter of Section IV): CholInv forms the inverse only for the diagonal
+  blocks below the top `depth` halvings; L21 and Q come from block forward
+  substitution (right_solve).
 
 Readings of points the paper leaves open (each also listed in the design notes):
 
@@ -105,14 +109,68 @@ def cholinv(W: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return _cholinv(W, 0)
 
 
-def cqr(A: np.ndarray) -> tuple[np.ndarray, np.ndarray, dict]:
+def right_solve(B: np.ndarray, L: np.ndarray, Y: np.ndarray, depth: int) -> np.ndarray:
+    """X = B L^-T for lower-triangular L whose inverse is known only on the
+    diagonal blocks of a depth-`depth` halving (Section III-A's alternative to
+    the full inverse: triangular inverted blocks, then Q by multiplications).
+
+    With L = [[L11, 0], [L21, L22]] the two block columns of X L^T = B give
+    X1 = B1 L11^-T and X2 = (B2 - X1 L21^T) L22^-T (block forward
+    substitution); at depth 0 Y is the full inverse and X = B Y^T.
+    """
+    n = L.shape[0]
+    if depth == 0 or n == 1:
+        return B @ Y.T
+    n1 = n // 2
+    X1 = right_solve(B[:, :n1], L[:n1, :n1], Y[:n1, :n1], depth - 1)
+    X2 = right_solve(B[:, n1:] - X1 @ L[n1:, :n1].T, L[n1:, n1:], Y[n1:, n1:], depth - 1)
+    return np.hstack([X1, X2])
+
+
+def _cholinv_depth(A: np.ndarray, offset: int, depth: int) -> tuple[np.ndarray, np.ndarray]:
+    # Algorithm 1 whose top `depth` recursion levels do not form Y21: the
+    # triangular inverse is computed only below that level (InverseDepth,
+    # Section IV), and L21 = A21 L11^-T comes from the block solve instead.
+    n = A.shape[0]
+    if depth == 0 or n == 1:
+        return _cholinv(A, offset)
+    n1 = n // 2
+    L11, Y11 = _cholinv_depth(A[:n1, :n1], offset, depth - 1)
+    L21 = right_solve(A[n1:, :n1], L11, Y11, depth - 1)
+    L22, Y22 = _cholinv_depth(A[n1:, n1:] - L21 @ L21.T, offset + n1, depth - 1)
+    L = np.zeros((n, n))
+    Y = np.zeros((n, n))  # Y21 is not formed
+    L[:n1, :n1] = L11
+    L[n1:, :n1] = L21
+    L[n1:, n1:] = L22
+    Y[:n1, :n1] = Y11
+    Y[n1:, n1:] = Y22
+    return L, Y
+
+
+def cholinv_depth(W: np.ndarray, depth: int) -> tuple[np.ndarray, np.ndarray]:
+    """[L, Y] of Algorithm 1 with inverse depth `depth`: L as before, Y holding
+    the inverses of L's diagonal blocks of the depth-`depth` halving only."""
+    W = np.asarray(W, dtype=np.float64)
+    if W.ndim != 2 or W.shape[0] != W.shape[1] or W.shape[0] < 1 or depth < 0:
+        raise ValueError("CholInv needs a non-empty square matrix and depth >= 0")
+    return _cholinv_depth(W, 0, depth)
+
+
+def cqr(A: np.ndarray, inverse_depth: int = 0) -> tuple[np.ndarray, np.ndarray, dict]:
     """[Q, R] = CQR(A) (Algorithm CQR, Section II-E).
 
     Returns Q, R and the intermediates {W, L, Y, Rinv}. R = L^T is upper
-    triangular and Rinv = Y^T = R^-1; Q = A R^-1.
+    triangular and Rinv = Y^T = R^-1; Q = A R^-1. With inverse_depth = d > 0
+    the inverse is formed only for the diagonal blocks of a depth-d halving
+    (cholinv_depth) and Q comes from right_solve; Rinv is then not returned.
     """
     A = np.asarray(A, dtype=np.float64)
     W = syrk(A)  # W = Syrk(A)
+    if inverse_depth:
+        L, Y = cholinv_depth(W, inverse_depth)
+        Q = right_solve(A, L, Y, inverse_depth)  # Q = A R^-1 by block forward substitution
+        return Q, np.ascontiguousarray(L.T), dict(W=W, L=L, Y=Y)
     L, Y = cholinv(W)  # R^T, R^-T = CholInv(W)
     R = np.ascontiguousarray(L.T)
     Rinv = np.ascontiguousarray(Y.T)
@@ -128,23 +186,23 @@ class PassFailed(NotSPD):
         self.pass_no = pass_no
 
 
-def cqr2(A: np.ndarray, keep: bool = False):
+def cqr2(A: np.ndarray, keep: bool = False, inverse_depth: int = 0):
     """[Q, R] = CQR2(A) (Algorithm CQR2, Section II-E).
 
     (Q1, R1) = CQR(A); (Q, R2) = CQR(Q1); R = R2 R1. With keep=True also
     returns a dict of intermediates (pass-1 and pass-2 W, L, Y, Rinv, Q1, R1,
-    R2).
+    R2). inverse_depth is passed to both CQR passes.
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     if m < n or n < 1:
         raise ValueError("CQR2 needs an m x n matrix with m >= n >= 1")
     try:
-        Q1, R1, i1 = cqr(A)
+        Q1, R1, i1 = cqr(A, inverse_depth)
     except NotSPD as e:
         raise PassFailed(1, e) from None
     try:
-        Q, R2, i2 = cqr(Q1)
+        Q, R2, i2 = cqr(Q1, inverse_depth)
     except NotSPD as e:
         raise PassFailed(2, e) from None
     R = np.triu(R2 @ R1)  # R = MM(R2, R1): a product of upper triangles is upper

@@ -328,3 +328,77 @@ def test_scqr3_needs_the_shift():
     exec(compile(src.replace(old, "    Ws = W"), "<mutant noshift>", "exec"), mod.__dict__)
     with pytest.raises(mod.NotSPD):
         mod.scqr3(A)
+
+
+# ------------------------------- inverse depth (Section III-A, InverseDepth)
+
+def _leaf_mask(n: int, depth: int) -> np.ndarray:
+    """True on the diagonal blocks of a depth-`depth` halving (split n // 2)."""
+    M = np.zeros((n, n), dtype=bool)
+
+    def rec(o, k, d):
+        if d == 0 or k == 1:
+            M[o:o + k, o:o + k] = True
+            return
+        k1 = k // 2
+        rec(o, k1, d - 1)
+        rec(o + k1, k - k1, d - 1)
+
+    rec(0, n, depth)
+    return M
+
+
+@pytest.mark.parametrize("n,depth", [(8, 1), (8, 3), (13, 2), (64, 4), (100, 3), (129, 5)])
+def test_cholinv_depth_minij_exact(n, depth):
+    # integer closed form: L = all-ones lower triangle exactly, and the inverse
+    # kept only on the leaf diagonal blocks (exact bidiagonal blocks of L^-1)
+    W, L, Y = minij(n)
+    Lo, Yo = oracle.cholinv_depth(W, depth)
+    np.testing.assert_array_equal(Lo, L)
+    np.testing.assert_array_equal(Yo, np.where(_leaf_mask(n, depth), Y, 0.0))
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 3, 6])
+def test_right_solve_defining_property(depth):
+    # X = B L^-T means X L^T = B; L and its inverse come from LAPACK, not the oracle
+    rng = np.random.default_rng(depth)
+    n, M = 150, 40
+    G = rng.standard_normal((n, n))
+    L = np.linalg.cholesky(G @ G.T + n * np.eye(n))
+    X = oracle.right_solve(rng.standard_normal((M, n)), L, np.linalg.inv(L), depth)
+    B = X @ L.T
+    assert np.linalg.norm(oracle.right_solve(B, L, np.linalg.inv(L), depth) - X) <= 1e-12 * np.linalg.norm(X)
+    B2 = rng.standard_normal((M, n))
+    X2 = oracle.right_solve(B2, L, np.linalg.inv(L), depth)
+    assert np.linalg.norm(X2 @ L.T - B2) <= 1e-13 * np.linalg.norm(B2)
+
+
+@pytest.mark.parametrize("m,n,kappa,depth", [(400, 64, 1e3, 1), (400, 64, 1e3, 3), (900, 150, 1e6, 2),
+                                             (300, 33, 1e4, 5)])
+def test_cqr2_depth_matches_householder(m, n, kappa, depth):
+    A = synth.make_matrix(m, n, kappa, seed=5)
+    Q, R = oracle.cqr2(A, inverse_depth=depth)
+    Qh, Rh = oracle.householder_qr(A)
+    tol = 10 * n * kappa * EPS
+    assert oracle.rel_error(R, Rh) <= tol
+    assert np.linalg.norm(Q - Qh) / math.sqrt(n) <= tol
+    assert oracle.orthogonality(Q) <= 100 * n * EPS
+
+
+def test_right_solve_planted_missing_update_is_caught():
+    # dropping the X1 L21^T term of the block substitution (a plausible slip)
+    src = inspect.getsource(ocq)
+    old = "    X2 = right_solve(B[:, n1:] - X1 @ L[n1:, :n1].T, L[n1:, n1:], Y[n1:, n1:], depth - 1)"
+    assert src.count(old) == 1
+    mod = types.ModuleType("oracle_mutant_noupdate")
+    exec(compile(src.replace(old, old.replace(" - X1 @ L[n1:, :n1].T", "")), "<mutant noupdate>", "exec"),
+         mod.__dict__)
+    W, L, Y = minij(20)
+    try:
+        Lm, _ = mod.cholinv_depth(W, 2)
+        assert not np.array_equal(Lm, L)
+    except mod.NotSPD:
+        pass  # the wrong Schur complement broke down: caught as well
+    B = np.random.default_rng(1).standard_normal((30, 20))
+    X = mod.right_solve(B, L, Y, 2)
+    assert np.linalg.norm(X @ L.T - B) > 1e-3 * np.linalg.norm(B)
