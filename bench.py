@@ -290,8 +290,11 @@ def bench_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
-    def make_plan(precision, fz):
-        return cq.Plan(m, n, precision=PRECISIONS[precision], fused=fz, stream=stream)
+    def make_plan(precision, fz, depth=0):
+        pl = cq.Plan(m, n, precision=PRECISIONS[precision], fused=fz, stream=stream)
+        if depth:
+            pl.set_inverse_depth(depth)
+        return pl
 
     def timed(pl, steps, warmup, profile):
         info = pl.factor(A, Q, R, sync=True)[2]
@@ -341,7 +344,7 @@ def bench_ours(args, ws, rank, local):
         return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
 
-    plan = make_plan(args.precision, fused)
+    plan = make_plan(args.precision, fused, args.inverse_depth)
     clocks = ClockSampler(local)
     clocks.start()
     ms_local, launches, per_stage = timed(plan, args.steps, args.warmup, True)
@@ -356,7 +359,7 @@ def bench_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-slices->f64",
         "data": "synthetic",
         "config": {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
-                   "variant": "fused" if fused else "plain",
+                   "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"},
         "gpu_launches": launches,
@@ -460,6 +463,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tall")
     ap.add_argument("--variant", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--inverse-depth", type=int, default=0,
+                    help="FP64, n > 256: CholInv levels without the off-diagonal inverse (block substitution)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64",
                     help="fp64: native FP64; ozaki / ozaki6: BF16 tensor-core slices (7 / 6 per entry)")
     ap.add_argument("--oracle-rows", type=int, default=None,

@@ -145,6 +145,21 @@ cqr2_status_t cqr2_lstsq_rows(cqr2_plan_t plan, int64_t m, const double* dA, int
 cqr2_status_t cqr2_plan_set_gram_ctas(cqr2_plan_t plan, int32_t ctas_per_sm);
 cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t plan, int32_t fused);
 
+/* Inverse depth (the paper's alternative of triangular inverted blocks,
+ * Section III-A "3D-CQR2", and its InverseDepth parameter, Section IV): with
+ * depth d > 0 the top d halvings of CholInv (Algorithm 1) do not form the
+ * off-diagonal inverse block Y21; L21 = A21 L11^-T and Q = A R^-1 are then
+ * computed by block forward substitution through the inverses of L's diagonal
+ * blocks (X1 = B1 L11^-T, X2 = (B2 - X1 L21^T) L22^-T). d = 0 (the default)
+ * forms the whole inverse. The result is the same factorization up to
+ * rounding, with less work in CholInv.
+ * Applies to native-FP64 plans with n > 256 (the general path); d > 0 on
+ * another plan returns CQR2_ERR_UNSUPPORTED, d outside 0..16
+ * CQR2_ERR_INVALID_ARG. The first d > 0 allocates an m x (about n/2) scratch
+ * buffer (CQR2_ERR_OOM if that fails). Not for use while the plan's stream
+ * has a call in flight. */
+cqr2_status_t cqr2_plan_set_inverse_depth(cqr2_plan_t plan, int32_t depth);
+
 /* Synchronize the plan's stream and report the outcome of the last
  * factorization enqueued on the plan. */
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info);

@@ -240,6 +240,12 @@ def cqr2_plan_set_fused(plan, fused: bool) -> None:
     N.check(N.load().cqr2_plan_set_fused(plan, 1 if fused else 0), "cqr2_plan_set_fused")
 
 
+def cqr2_plan_set_inverse_depth(plan, depth: int) -> None:
+    """Triangular inverse only on the diagonal blocks below the top `depth`
+    halvings of CholInv; L21 and Q by block forward substitution."""
+    N.check(N.load().cqr2_plan_set_inverse_depth(plan, int(depth)), "cqr2_plan_set_inverse_depth")
+
+
 def cqr2_autotune(m: int, n: int, precision: int = CQR2_FP64) -> dict:
     """Time candidate plan configurations for an m x n factorization and
     record the best in the library's tuning table."""
@@ -344,6 +350,9 @@ class Plan:
 
     def set_gram_ctas(self, ctas_per_sm: int) -> None:
         cqr2_plan_set_gram_ctas(self.handle, ctas_per_sm)
+
+    def set_inverse_depth(self, depth: int) -> None:
+        cqr2_plan_set_inverse_depth(self.handle, depth)
 
     def set_fused(self, fused: bool) -> None:
         cqr2_plan_set_fused(self.handle, fused)

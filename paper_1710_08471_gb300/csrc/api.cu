@@ -22,6 +22,9 @@ struct cqr2_plan_st {
   int64_t cm = 0;        // row count of the call in progress (geometry below is for cm)
   int gram_cps = 4;      // Gram CTAs per SM (autotuned knob, 1..GRAM_CPS_MAX)
   int64_t gram_cap = 0;  // row ranges the Gram partials have room for (any cm <= m)
+  int inv_depth = 0;         // CholInv levels without Y21 (0: whole inverse)
+  double* Tsolve = nullptr;  // block-substitution scratch, ldt x right_solve_temp_cols(n)
+  int64_t ldt = 0;
   int64_t oz_cap = 0;    // same for the split-precision Gram partials
   int precision = CQR2_FP64;
   unsigned flags = 0;
@@ -164,6 +167,25 @@ cudaError_t hx_wait_input(cqr2_plan_st* p, cudaStream_t s) {
   return cudaStreamWaitEvent(s, p->hx_ev[HX_BLOCKS - 1], 0);
 }
 
+// [L, Y] = CholInv(W) of the plan's pass, with the plan's inverse depth.
+cudaError_t plan_cholinv(cqr2_plan_st* p, int pass, cudaStream_t s) {
+  const int n = (int)p->n;
+  if (p->inv_depth > 0)
+    return cholinv_depth(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->Tsolve, p->ldt, p->st, pass, p->inv_depth,
+                         s);
+  return cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s);
+}
+
+// X = B R^-1 = B L^-T (general path, rows x n): one triangular multiply by
+// the whole inverse, or block forward substitution at inverse depth d > 0.
+cudaError_t plan_apply_rinv(cqr2_plan_st* p, int64_t rows, const double* B, int64_t ldb, double* X, int64_t ldx,
+                            cudaStream_t s) {
+  const int n = (int)p->n;
+  if (p->inv_depth > 0)
+    return right_solve(rows, n, B, ldb, X, ldx, p->L, n, p->Y, n, p->inv_depth, p->Tsolve, p->ldt, s);
+  return gemm_f64(rows, n, n, 1.0, B, ldb, p->Y, n, 0.0, X, ldx, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s);
+}
+
 cqr2_status_t read_info(cqr2_plan_st* p, cqr2_info_t* info) {
   TRY(cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, p->stream));
   TRY(cudaStreamSynchronize(p->stream));
@@ -276,7 +298,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
-    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + 1, s));
+    TRY(plan_cholinv(p, pass_base + 1, s));
     TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
   }
   // ---- Q1 = A R1^-1 (staged in dQ on the small path), then pass 2 on Q1
@@ -293,7 +315,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
     }
   } else {
     Stage st(p, CQR2_STAGE_QFORM1);
-    TRY(gemm_f64(p->cm, n, n, 1.0, dA, lda, p->Y, n, 0.0, p->Q1, p->m, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+    TRY(plan_apply_rinv(p, p->cm, dA, lda, p->Q1, p->m, s));
     X2 = p->Q1;
     ldx2 = p->m;
   }
@@ -304,7 +326,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV2);
-    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + 2, s));
+    TRY(plan_cholinv(p, pass_base + 2, s));
   }
   {
     Stage st(p, CQR2_STAGE_QFORM2);
@@ -318,8 +340,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
         if (p->small) {
           TRY(qform_small(dQ + r0, ldq, r1 - r0, n, p->Rp, dQ + r0, ldq, s));  // in place, panel by panel
         } else {
-          TRY(gemm_f64(r1 - r0, n, n, 1.0, X2 + r0, ldx2, p->Y, n, 0.0, dQ + r0, ldq,
-                       GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+          TRY(plan_apply_rinv(p, r1 - r0, X2 + r0, ldx2, dQ + r0, ldq, s));
         }
       }
       if (p->hx.on) {
@@ -369,7 +390,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
-    TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, 1, s));
+    TRY(plan_cholinv(p, 1, s));
     TRY(transpose_lower(p->L, n, n, p->R0, n, s));  // R0 = L0^T
   }
   {
@@ -382,7 +403,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
       TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
       TRY(qform_small(dA, lda, m, n, p->Rp, dQ, ldq, s));
     } else {
-      TRY(gemm_f64(m, n, n, 1.0, dA, lda, p->Y, n, 0.0, dQ, ldq, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s));
+      TRY(plan_apply_rinv(p, m, dA, lda, dQ, ldq, s));
     }
   }
   cqr2_status_t r = factor_impl(p, dQ, ldq, dQ, ldq, p->Rt, n, 1);
@@ -566,6 +587,7 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
   }
   for (cudaEvent_t e : plan->hx_ev) cudaEventDestroy(e);
   cudaFree(plan->hx_partial);
+  cudaFree(plan->Tsolve);
   cudaFree(plan->hA_dev);
   cudaFree(plan->hQ_dev);
   cudaFree(plan->hR_dev);
@@ -633,6 +655,26 @@ cqr2_status_t cqr2_plan_set_gram_ctas(cqr2_plan_t p, int32_t ctas_per_sm) {
   p->gram_cps = ctas_per_sm;
   p->cm = 0;  // recompute the geometry on the next call
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_plan_set_inverse_depth(cqr2_plan_t p, int32_t depth) {
+  if (!p || depth < 0 || depth > 16) return CQR2_ERR_INVALID_ARG;
+  if (depth > 0 && (p->oz_S || p->small)) return CQR2_ERR_UNSUPPORTED;
+  if (depth > 0 && !p->Tsolve) {
+    const int64_t ldt = std::max(p->m, p->n);
+    if (cudaMalloc(&p->Tsolve, (size_t)ldt * right_solve_temp_cols((int)p->n) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      p->Tsolve = nullptr;
+      return CQR2_ERR_OOM;
+    }
+    p->ldt = ldt;
+  }
+  p->inv_depth = depth;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);  // a captured launch sequence no longer applies
   if (p->graph) cudaGraphDestroy(p->graph);
   p->gexec = nullptr;
   p->graph = nullptr;

@@ -125,7 +125,84 @@ cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* 
   return gemm_f64(n2, n1, n2, -1.0, Y22, ldy, U, ldu, 0.0, Y + n1, ldy, GEMM_A_LOWER | GEMM_BETA0, s);
 }
 
+// Depth-limited recursion: the top `depth` levels form L21 by block forward
+// substitution through the diagonal blocks' inverses and leave Y21 zero.
+cudaError_t rec_depth(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
+                      int64_t ldu, double* T, int64_t ldt, DevStatus* st, int pass, long long off, int depth,
+                      cudaStream_t s) {
+  if (depth <= 0 || n <= NB) return rec(n, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s);
+  const int n1 = NB * (int)ceil_div(n, 2 * NB);
+  const int n2 = n - n1;
+  cudaError_t e;
+  // [L11, Y11] with Y11 known on its leaf blocks only
+  if ((e = rec_depth(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, T, ldt, st, pass, off, depth - 1, s)) != cudaSuccess)
+    return e;
+  // L21 = W21 L11^-T
+  if ((e = right_solve(n2, n1, Wk + n1, ldk, L + n1, ldl, L, ldl, Y, ldy, depth - 1, T, ldt, s)) != cudaSuccess)
+    return e;
+  // W22 <- W22 - L21 L21^T (lower triangle)
+  double* W22 = Wk + n1 + (int64_t)n1 * ldk;
+  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s)) !=
+      cudaSuccess)
+    return e;
+  return rec_depth(n2, W22, ldk, L + n1 + (int64_t)n1 * ldl, ldl, Y + n1 + (int64_t)n1 * ldy, ldy, U, ldu, T, ldt,
+                   st, pass, off + n1, depth - 1, s);
+}
+
 }  // namespace
+
+cudaError_t right_solve(int64_t M, int N, const double* B, int64_t ldb, double* X, int64_t ldx, const double* L,
+                        int64_t ldl, const double* Y, int64_t ldy, int depth, double* T, int64_t ldt,
+                        cudaStream_t s) {
+  cudaError_t e;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (depth <= 0 || N <= NB) {
+    // X = B Y^T with Y the inverse of this diagonal block (Y^T upper triangular)
+    if ((const double*)X != B)
+      return gemm_f64(M, N, N, 1.0, B, ldb, Y, ldy, 0.0, X, ldx, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s);
+    if ((e = gemm_f64(M, N, N, 1.0, B, ldb, Y, ldy, 0.0, T, ldt, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0, s)) !=
+        cudaSuccess)
+      return e;
+    return cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), T, (size_t)ldt * sizeof(double),
+                             (size_t)M * sizeof(double), (size_t)N, cudaMemcpyDeviceToDevice, s);
+  }
+  // the split of the recursion that formed Y, so the leaves are its inverted blocks
+  const int n1 = NB * (int)ceil_div(N, 2 * NB);
+  const int n2 = N - n1;
+  // X1 = B1 L11^-T
+  if ((e = right_solve(M, n1, B, ldb, X, ldx, L, ldl, Y, ldy, depth - 1, T, ldt, s)) != cudaSuccess) return e;
+  // X2 = (B2 - X1 L21^T) L22^-T, the bracket formed in X2
+  double* X2 = X + (int64_t)n1 * ldx;
+  if ((const double*)X != B &&
+      (e = cudaMemcpy2DAsync(X2, (size_t)ldx * sizeof(double), B + (int64_t)n1 * ldb, (size_t)ldb * sizeof(double),
+                             (size_t)M * sizeof(double), (size_t)n2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = gemm_f64(M, n2, n1, -1.0, X, ldx, L + n1, ldl, 1.0, X2, ldx, GEMM_TB, s)) != cudaSuccess) return e;
+  return right_solve(M, n2, X2, ldx, X2, ldx, L + n1 + (int64_t)n1 * ldl, ldl, Y + n1 + (int64_t)n1 * ldy, ldy,
+                     depth - 1, T, ldt, s);
+}
+
+int right_solve_temp_cols(int n) { return n <= NB ? n : NB * (int)ceil_div(n, 2 * NB); }
+
+cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
+                          double* work, double* U, double* T, int64_t ldt, DevStatus* st, int pass, int depth,
+                          cudaStream_t s) {
+  if (depth <= 0) return cholinv(n, W, ldw, L, ldl, Y, ldy, work, U, st, pass, s);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_cholinv_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BASE_SMEM)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpy2DAsync(work, (size_t)n * sizeof(double), W, (size_t)ldw * sizeof(double),
+                             (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemset2DAsync(L, (size_t)ldl * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
+      cudaSuccess)
+    return e;
+  return rec_depth(n, work, n, L, ldl, Y, ldy, U, n, T, ldt, st, pass, 0, depth, s);
+}
 
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                     double* work, double* U, DevStatus* st, int pass, cudaStream_t s) {

@@ -76,6 +76,20 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
 constexpr int CHOLINV_BASE = 64;
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                     double* work, double* U, DevStatus* st, int pass, cudaStream_t s);
+// Inverse depth (the paper's triangular inverted blocks): the top `depth`
+// halvings form L21 = W21 L11^-T by block forward substitution and leave Y21
+// zero, so Y holds the inverses of L's diagonal blocks only. T is scratch of
+// n x right_solve_temp_cols(n) doubles (ld ldt >= n).
+cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
+                          double* work, double* U, double* T, int64_t ldt, DevStatus* st, int pass, int depth,
+                          cudaStream_t s);
+// X = B L^-T (M x N) for lower-triangular L whose diagonal-block inverses of a
+// depth-`depth` halving are in Y: X1 = B1 L11^-T, X2 = (B2 - X1 L21^T) L22^-T.
+// X may equal B. T is scratch of M x right_solve_temp_cols(N) (ld ldt >= M).
+cudaError_t right_solve(int64_t M, int N, const double* B, int64_t ldb, double* X, int64_t ldx, const double* L,
+                        int64_t ldl, const double* Y, int64_t ldy, int depth, double* T, int64_t ldt,
+                        cudaStream_t s);
+int right_solve_temp_cols(int n);
 // Shifted CholeskyQR: W += s I, s = 11 (m n + n (n+1)) 2^-53 trace(W).
 cudaError_t add_shift(double* W, int64_t ldw, int n, int64_t m, cudaStream_t s);
 // R = L^T (upper) with zeros below the diagonal.
