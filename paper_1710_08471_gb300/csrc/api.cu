@@ -76,7 +76,6 @@ struct cqr2_plan_st {
   unsigned short* oz_rinv = nullptr;
   unsigned long long* oz_colmax = nullptr;
   int* oz_cexp = nullptr;
-  int* oz_rexp = nullptr;
   int* oz_fexp = nullptr;
   double* oz_partial = nullptr;
   OzMaps oz_maps;
@@ -247,13 +246,12 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, CQR2_STAGE_SPLIT);
-      TRY(ozaki_slice_rinv(p->Y, n, n, S, false, p->oz_rinv, p->oz_fexp, s));
-      TRY(ozaki_slice_rows(X, ldx, m, n, S, p->oz_planes, p->oz_rexp, s));
+      TRY(ozaki_slice_rinv(p->Y, n, n, S, false, p->oz_cexp, p->oz_rinv, p->oz_fexp, s));
     }
     {
       // The Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
       Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
-      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, s));
+      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_fexp, dQ, ldq, p->st, s));
     }
   }
   {
@@ -396,9 +394,8 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   {
     Stage st(p, CQR2_STAGE_QFORM1);
     if (p->oz_S) {
-      TRY(ozaki_slice_rinv(p->Y, n, n, p->oz_S, false, p->oz_rinv, p->oz_fexp, s));
-      TRY(ozaki_slice_rows(dA, lda, m, n, p->oz_S, p->oz_planes, p->oz_rexp, s));
-      TRY(ozaki_qform(p->oz_maps, m, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, s));
+      TRY(ozaki_slice_rinv(p->Y, n, n, p->oz_S, false, p->oz_cexp, p->oz_rinv, p->oz_fexp, s));
+      TRY(ozaki_qform(p->oz_maps, m, n, p->oz_S, p->oz_fexp, dQ, ldq, p->st, s));
     } else if (p->small) {
       TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
       TRY(qform_small(dA, lda, m, n, p->Rp, dQ, ldq, s));
@@ -504,7 +501,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
     take((size_t)oz_S * n * og.np * 2);                              // 15 R^-1 planes
     take((size_t)n * sizeof(unsigned long long));                    // 16 column max
     take((size_t)n * sizeof(int));                                   // 17 column exponents
-    take((size_t)m * sizeof(int));                                   // 18 row exponents
+    take(0);                                                         // 18 (unused)
     take((size_t)n * sizeof(int));                                   // 19 R^-1 exponents
     take((size_t)p->oz_cap * n * n * sizeof(double));                // 20 Gram partials
   }
@@ -540,7 +537,6 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
     p->oz_rinv = reinterpret_cast<unsigned short*>(p->ws + off[15]);
     p->oz_colmax = reinterpret_cast<unsigned long long*>(p->ws + off[16]);
     p->oz_cexp = reinterpret_cast<int*>(p->ws + off[17]);
-    p->oz_rexp = reinterpret_cast<int*>(p->ws + off[18]);
     p->oz_fexp = reinterpret_cast<int*>(p->ws + off[19]);
     p->oz_partial = at(20);
     // zero the planes once so that padding rows/columns read as zero
@@ -766,9 +762,10 @@ cqr2_status_t cqr2_qform(cqr2_plan_t p, const double* dA, int64_t lda, const dou
   const int n = (int)p->n;
   if (p->oz_S) {
     TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
-    TRY(ozaki_slice_rinv(dRinv, ldri, n, p->oz_S, true, p->oz_rinv, p->oz_fexp, p->stream));
-    TRY(ozaki_slice_rows(dA, lda, p->cm, n, p->oz_S, p->oz_planes, p->oz_rexp, p->stream));
-    TRY(ozaki_qform(p->oz_maps, p->cm, n, p->oz_S, p->oz_rexp, p->oz_fexp, dQ, ldq, p->st, p->stream));
+    TRY(ozaki_colmax(dA, lda, p->cm, n, p->oz_colmax, p->oz_cexp, p->stream));
+    TRY(ozaki_slice_cols(dA, lda, p->cm, n, p->oz_S, p->oz_cexp, p->oz_planes, p->stream));
+    TRY(ozaki_slice_rinv(dRinv, ldri, n, p->oz_S, true, p->oz_cexp, p->oz_rinv, p->oz_fexp, p->stream));
+    TRY(ozaki_qform(p->oz_maps, p->cm, n, p->oz_S, p->oz_fexp, dQ, ldq, p->st, p->stream));
   } else if (p->small) {
     TRY(pack_rinv_from_upper(dRinv, ldri, n, p->Rp, p->stream));
     TRY(qform_small(dA, lda, p->cm, n, p->Rp, dQ, ldq, p->stream));

@@ -112,7 +112,7 @@ struct OzGeom {
 struct OzMaps {
   alignas(64) unsigned char col_a[128];
   alignas(64) unsigned char col_b[128];
-  alignas(64) unsigned char row_a[128];
+  alignas(64) unsigned char col_a_mn[128];  // the column slices as the Q-form's MN-major left operand
   alignas(64) unsigned char rinv_b[128];
 };
 bool ozaki_supported(int n, int S);
@@ -125,15 +125,15 @@ cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned
                          cudaStream_t s);
 cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int S, const int* cexp,
                              unsigned short* planes, cudaStream_t s);
-cudaError_t ozaki_slice_rows(const double* X, int64_t ld, int64_t m, int n, int S, unsigned short* planes, int* rexp,
-                             cudaStream_t s);
-cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, unsigned short* planes,
-                             int* fexp, cudaStream_t s);
+// R^-1 slices with X's column exponents cexp folded into its rows (cexp may be null).
+cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, const int* cexp,
+                             unsigned short* planes, int* fexp, cudaStream_t s);
 // partial holds max_splits n x n blocks; a geometry needing more is refused.
 cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
                        int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s);
-cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* rexp, const int* fexp, double* Q,
-                        int64_t ldq, DevStatus* st, cudaStream_t s);
+// Q = X R^-1 from X's column slices (the Gram's planes) and R^-1's slices.
+cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
+                        DevStatus* st, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched
 // One problem of a grouped launch (same layout as cqr2_problem_t).

@@ -32,6 +32,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "kernels.h"
 #include "oz_fixed.cuh"
@@ -179,85 +180,45 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ X
   }
 }
 
-// Row slices for the Q-form's left operand: planes[s][r][k], k < np, with one
-// exponent per row. A CTA stages RB rows x n in shared memory (read
-// coalesced down the columns), finds each row's largest entry, and writes
-// four consecutive k per thread (one 8-byte store per slice).
-template <int S, int RB>
-__global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ X, int64_t ld, int64_t m, int n, int np,
-                                                    unsigned short* __restrict__ planes, int* __restrict__ rexp) {
-  extern __shared__ double tile[];  // [n][RB + 1]
-  __shared__ int sexp[RB];
-  constexpr int LDT = RB + 1;
-  const int64_t r0 = (int64_t)blockIdx.x * RB;
-  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
-    const int r = e % RB, k = e / RB;
-    tile[k * LDT + r] = (r0 + r < m) ? X[r0 + r + (int64_t)k * ld] : 0.0;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < RB; r += 8) {
-    unsigned long long mx = 0;
-    for (int k = lane; k < n; k += 32) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(tile[k * LDT + r]) & 0x7FFFFFFFFFFFFFFFull;
-      mx = b > mx ? b : mx;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = v > mx ? v : mx;
-    }
-    if (lane == 0) {
-      sexp[r] = exp_from_bits(mx);
-      if (r0 + r < m) rexp[r0 + r] = sexp[r];
-    }
-  }
-  __syncthreads();
-  const size_t stride = (size_t)m * np;
-  const int q4 = np / 4;
-  for (int e = threadIdx.x; e < RB * q4; e += blockDim.x) {
-    const int r = e / q4, k = 4 * (e % q4);
-    if (r0 + r >= m) continue;
-    double x[4];
-    int ex[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      x[q] = k + q < n ? tile[(k + q) * LDT + r] : 0.0;
-      ex[q] = sexp[r];
-    }
-    write_digits4<S>(x, ex, planes + (size_t)(r0 + r) * np + k, stride);
-  }
-}
-
-// Slices of R^-1 = Y^T for the Q-form's right operand: planes[s][j][k] holds
-// R^-1(k, j) = Y(j, k) for k <= j, one exponent per column j of R^-1.
-// With from_upper the input is R^-1 itself (upper triangular, R^-1(k, j) at
-// Y[k + j * ldy]) instead of Y = (R^-1)^T.
+// Right operand of the Q-form, R^-1 in slices planes[s][j][k] (k < np). The
+// left operand is X in its column slices, x(i,k) = 2^c_k xt(i,k) with the
+// Gram's column exponents c_k; the scale 2^c_k moves into row k of R^-1
+// (exact), r'(k,j) = 2^c_k r(k,j), so that the contraction over k has one
+// exponent per column j of R^-1: f_j = max_k (c_k + e(r(k,j))) over the
+// nonzero entries, and r'(k,j) is cut with exponent f_j (digits of r(k,j) with
+// exponent f_j - c_k). cexp == nullptr means c_k = 0. With from_upper the
+// input is R^-1 itself (upper triangular, R^-1(k, j) at Y[k + j * ldy])
+// instead of Y = (R^-1)^T.
 template <int S>
 __global__ void __launch_bounds__(256) k_slice_rinv(const double* __restrict__ Y, int64_t ldy, int n, int np,
-                                                    bool from_upper, unsigned short* __restrict__ planes,
-                                                    int* __restrict__ fexp) {
+                                                    bool from_upper, const int* __restrict__ cexp,
+                                                    unsigned short* __restrict__ planes, int* __restrict__ fexp) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + warp;
   if (j >= n) return;
   const int64_t sj = from_upper ? (int64_t)j * ldy : (int64_t)j;  // offset of (j, 0) in Y-coordinates
   const int64_t sk = from_upper ? 1 : ldy;                        // stride along k
-  unsigned long long mx = 0;
+  int f = INT_MIN;
   for (int k = lane; k <= j; k += 32) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(Y[sj + k * sk]) & 0x7FFFFFFFFFFFFFFFull;
-    mx = b > mx ? b : mx;
+    if (b == 0) continue;
+    const int ck = cexp ? cexp[k] : 0;
+    const int e = exp_from_bits(b);
+    const int ef = (e >= EXP_NONFINITE || ck >= EXP_NONFINITE) ? EXP_NONFINITE : e + ck;
+    f = ef > f ? ef : f;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = v > mx ? v : mx;
+    const int v = __shfl_xor_sync(0xffffffffu, f, o);
+    f = v > f ? v : f;
   }
-  const int e = exp_from_bits(mx);
-  if (lane == 0) fexp[j] = e;
+  if (f == INT_MIN) f = 0;  // an all-zero column
+  if (lane == 0) fexp[j] = f;
   const size_t stride = (size_t)n * np;
   for (int k = lane; k < np; k += 32) {
     const double x = k <= j ? Y[sj + k * sk] : 0.0;
-    write_digits<S>(x, e, planes + (size_t)j * np + k, stride);
+    const int ck = cexp && k < n ? cexp[k] : 0;
+    write_digits<S>(x, f >= EXP_NONFINITE ? EXP_NONFINITE : f - ck, planes + (size_t)j * np + k, stride);
   }
 }
 
@@ -307,6 +268,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
           smem_u32(dst)),
       "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
+}
+// MN-major operand (the Q-form's X tile, [k][m] rows of 64 m-values): 128-byte
+// swizzle, 64-element atoms along M 8192 bytes apart (the two TMA boxes), 8-row
+// groups along K 1024 bytes apart; 16 k further is 2048 bytes.
+__device__ __forceinline__ uint64_t sdesc_mn(const void* p) {
+  const uint64_t a = (smem_u32(p) & 0x3FFFF) >> 4;
+  return a | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
@@ -373,8 +341,8 @@ struct OzParams {
   int ntile_j;             // column tiles, ceil(n / BN)
   int ntiles;              // Gram: tiles touching the upper triangle
   int64_t nitems;          // work items (tiles x row ranges, or output tiles)
-  const int* eA;           // Gram: column exponents; Q-form: row exponents of X
-  const int* eB;           // Gram: column exponents; Q-form: column exponents of R^-1
+  const int* eA;           // Gram: column exponents; Q-form: unused (null)
+  const int* eB;           // Gram: column exponents; Q-form: column exponents of the scaled R^-1
   double* out;             // Gram: partial[split][n][n]; Q-form: Q
   int64_t ldo;
   DevStatus* st;
@@ -570,7 +538,12 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           for (int s = 0; s < S; ++s) {
             if (awrapped && !(ok = mbar_wait(&aempty[slot], aph ^ 1u, p.st))) break;
             mbar_expect_tx(&afull[slot], A_BYTES);
-            tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)w.i0, s);
+            if (MODE == OZ_GRAM) {
+              tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)w.i0, s);
+            } else {  // X read from its column slices: two 64-row boxes, m innermost
+              tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], (int)w.i0, k0, s);
+              tma_load_3d(sA + slot * A_BYTES + A_BYTES / 2, &tA, &afull[slot], (int)w.i0 + OZ_BM / 2, k0, s);
+            }
             if (++slot == NA) {
               slot = 0;
               aph ^= 1u;
@@ -588,8 +561,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // kind::f16, BF16 A and B, FP32 accumulate, both K-major, M = 128
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
+      // kind::f16, BF16 A and B, FP32 accumulate, M = 128; B K-major; A K-major
+      // (Gram) or MN-major (Q-form, bit 15)
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (MODE == OZ_QFORM ? 1u << 15 : 0u) |
+                             ((uint32_t)(OZ_BM >> 4) << 24);
       bool ok = true;
       int slot = 0, buf = 0;
       uint32_t aph = 0, bph = 0;
@@ -616,7 +591,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           for (int s = 0; s < S; ++s) {
             if (!(ok = mbar_wait(&afull[slot], aph, p.st))) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint64_t da = sdesc(sA + slot * A_BYTES);
+            const uint64_t da = MODE == OZ_GRAM ? sdesc(sA + slot * A_BYTES) : sdesc_mn(sA + slot * A_BYTES);
+            constexpr uint64_t DA_K16 = MODE == OZ_GRAM ? 2 : 2048 >> 4;  // descriptor step per 16 k
             // Products (s, t), t = t0 .. t0+nt-1, in one MMA of N = BN nt: the
             // B slices lie back to back in shared memory (one 1024-byte pitch
             // per 8 rows throughout) and group g = s + t is the BN-column
@@ -636,7 +612,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
               const uint32_t d = acc + (uint32_t)((s + t0) * BN);
               mma_bf16(d, da, db, idesc_n, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
-              for (int k = 1; k < OZ_BK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc_n, 1u);
+              for (int k = 1; k < OZ_BK / 16; ++k) mma_bf16(d, da + DA_K16 * k, db + 2 * k, idesc_n, 1u);
             }
             if (!ok) break;
             mma_commit(&aempty[slot]);
@@ -673,8 +649,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       for (int c = 0; c < CPT; ++c) X[c] = Y[c] = 0;
       const int64_t row = w.i0 + q4 * 32 + lane;
       const int64_t nrow = MODE == OZ_GRAM ? p.n : p.m;
-      // Q-form items are short: load the row exponent now, off the conversion's path
-      const int ea = MODE == OZ_QFORM && row < nrow ? p.eA[row] : 0;
+      const int ea = 0;  // Q-form: X's column exponents live in R^-1's slices
       for (int c = 0; c < nchunks && ok; ++c, ++gc) {
         const int ab = NGRP == 2 ? grp : (int)(gc % NBUF);
         const uint32_t par = (uint32_t)((NGRP == 2 ? gc : gc / NBUF) & 1);
@@ -815,7 +790,7 @@ int64_t ozaki_split_capacity(int64_t m, int n) {
 
 size_t ozaki_plane_elems(int64_t m, int n, int S) {
   const OzGeom g = ozaki_geometry(m, n);
-  return (size_t)S * std::max<size_t>((size_t)n * g.mp, (size_t)m * g.np);
+  return (size_t)S * n * g.mp;
 }
 
 cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes, void* rinv_planes) {
@@ -834,7 +809,7 @@ cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes,
   static_assert(sizeof(CUtensorMap) <= sizeof(OzMaps::col_a), "tensor map storage");
   bool ok = make((CUtensorMap*)maps.col_a, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BM) &&
             make((CUtensorMap*)maps.col_b, planes, (uint64_t)g.mp, (uint64_t)n, OZ_GRAM_BN) &&
-            make((CUtensorMap*)maps.row_a, planes, (uint64_t)g.np, (uint64_t)m, OZ_BM) &&
+            make((CUtensorMap*)maps.col_a_mn, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BK) &&
             make((CUtensorMap*)maps.rinv_b, rinv_planes, (uint64_t)g.np, (uint64_t)n, OZ_QFORM_BN);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -862,34 +837,13 @@ cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int 
   return cudaGetLastError();
 }
 
-template <int S, int RB>
-cudaError_t launch_slice_rows(const double* X, int64_t ld, int64_t m, int n, int np, unsigned short* planes, int* rexp,
-                              cudaStream_t s) {
-  const size_t sm = (size_t)n * (RB + 1) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_slice_rows<S, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_slice_rows<S, RB><<<(unsigned)ceil_div(m, RB), 256, sm, s>>>(X, ld, m, n, np, planes, rexp);
-  count_launch();
-  return cudaGetLastError();
-}
 
-cudaError_t ozaki_slice_rows(const double* X, int64_t ld, int64_t m, int n, int S, unsigned short* planes, int* rexp,
-                             cudaStream_t s) {
-  const OzGeom g = ozaki_geometry(m, n);
-  // 32 rows per CTA while the staged tile fits (n <= 512), else 16
-  if (n <= 512)
-    return S == 7 ? launch_slice_rows<7, 32>(X, ld, m, n, g.np, planes, rexp, s)
-                  : launch_slice_rows<6, 32>(X, ld, m, n, g.np, planes, rexp, s);
-  return S == 7 ? launch_slice_rows<7, 16>(X, ld, m, n, g.np, planes, rexp, s)
-                : launch_slice_rows<6, 16>(X, ld, m, n, g.np, planes, rexp, s);
-}
-
-cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, unsigned short* planes,
-                             int* fexp, cudaStream_t s) {
+cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, const int* cexp,
+                             unsigned short* planes, int* fexp, cudaStream_t s) {
   const int np = (int)(ceil_div(n, OZ_BK) * OZ_BK);
   const unsigned grid = (unsigned)ceil_div(n, 8);
-  if (S == 7) k_slice_rinv<7><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, planes, fexp);
-  else k_slice_rinv<6><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, planes, fexp);
+  if (S == 7) k_slice_rinv<7><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp);
+  else k_slice_rinv<6><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp);
   count_launch();
   return cudaGetLastError();
 }
@@ -922,13 +876,13 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
   return cudaGetLastError();
 }
 
-cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* rexp, const int* fexp, double* Q,
-                        int64_t ldq, DevStatus* st, cudaStream_t s) {
+cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
+                        DevStatus* st, cudaStream_t s) {
   const OzGeom g = ozaki_geometry(m, n);
   OzParams p{};
   p.m = m;
   p.n = n;
-  p.eA = rexp;
+  p.eA = nullptr;  // X enters through its column slices, whose exponents are folded into R^-1
   p.eB = fexp;
   p.out = Q;
   p.ldo = ldq;
@@ -937,7 +891,7 @@ cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* 
   p.ntiles = 1;
   p.nitems = (int64_t)p.ntile_j * ceil_div(m, OZ_BM);
   dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
-  const CUtensorMap& a = *(const CUtensorMap*)maps.row_a;
+  const CUtensorMap& a = *(const CUtensorMap*)maps.col_a_mn;
   const CUtensorMap& b = *(const CUtensorMap*)maps.rinv_b;
   return S == 7 ? launch_oz<7, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s)
                 : launch_oz<6, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s);

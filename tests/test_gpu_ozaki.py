@@ -82,9 +82,12 @@ def test_ozaki_qform(cq, m, n, kappa, S, prec):
     with cq.Plan(m, n, precision=prec) as p:
         Q = to_host(p.qform(to_dev(A), to_dev(garbage)))
     Qo = A @ Rinv
-    re = pow2_above(np.max(np.abs(A), axis=1))
-    fe = pow2_above(np.max(np.abs(Rinv), axis=0))
-    bound = n * np.outer(re, fe) * 2.0 ** (2 - frac_bits(S)) + 2 * n * EPS * (np.abs(A) @ np.abs(Rinv))
+    # X enters through its column slices (exponent c_k per column, the Gram's),
+    # with 2^c_k folded into row k of R^-1: one exponent f_j per column of the
+    # scaled R^-1, and every product's truncation is below 2^(f_j - frac + 1)
+    ce = pow2_above(np.max(np.abs(A), axis=0))
+    fe = pow2_above(np.max(ce[:, None] * np.abs(np.triu(Rinv)), axis=0))
+    bound = n * fe[None, :] * 2.0 ** (2 - frac_bits(S)) + 2 * n * EPS * (np.abs(A) @ np.abs(Rinv))
     assert np.all(np.abs(Q - Qo) <= bound), float(np.max(np.abs(Q - Qo) / bound))
 
 
