@@ -398,7 +398,7 @@ def bench_ours(args, ws, rank, local):
         todo = [("fp64", not fused), ("ozaki", False), ("ozaki6", False)] if args.precision == "fp64" else \
             [("fp64", True)] + [(p, False) for p in ("ozaki", "ozaki6") if p != args.precision]
         for prec, fz in todo:
-            if SLICES[prec] and n > 1024:
+            if SLICES[prec] and n > 16384:
                 continue
             name = prec + ("_fused" if fz and prec == "fp64" else "")
             try:

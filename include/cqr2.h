@@ -59,7 +59,7 @@ typedef enum {
  * CQR2_OZAKI_BF16: the Gram and Q-forming products are emulated on the
  *   BF16 tensor cores from 7 error-free slices of every FP64 entry (about 55
  *   significant bits, Ozaki scheme) with exact accumulation; CholInv and
- *   R = R2 R1 stay native FP64. Not part of the paper. n <= 1024.
+ *   R = R2 R1 stay native FP64. Not part of the paper. n <= 16384.
  * CQR2_OZAKI_BF16_S6: the same with 6 slices (about 47 bits): faster, with
  *   errors within 10x of the FP64 bounds for kappa(A) <= 1e6. */
 typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2_precision_t;

@@ -99,7 +99,7 @@ cudaError_t copy_upper(const double* X, int64_t ldx, int n, double* R, int64_t l
 
 // ---------------------------------------------------------------- Ozaki
 // Split-precision Gram and Q-form on BF16 tensor cores (see ozaki.cu).
-constexpr int OZAKI_MAX_N = 1024;
+constexpr int OZAKI_MAX_N = 16384;
 struct OzGeom {
   int64_t mp = 0;            // m rounded up to 64
   int np = 0;                // n rounded up to 64

@@ -147,5 +147,15 @@ def test_ozaki_nan_reports_not_spd(cq):
 
 def test_ozaki_rejects_large_n(cq):
     with pytest.raises(cq.CQR2Error) as e:
-        cq.Plan(5000, 1100, precision=cq.CQR2_OZAKI_BF16)
+        cq.Plan(17000, 16385, precision=cq.CQR2_OZAKI_BF16)
     assert e.value.status == cq.CQR2_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("m,n,kappa", [(8192, 2048, 1e4), (6000, 4100, 1e3)])
+def test_ozaki_cqr2_large_n(cq, m, n, kappa):
+    # near-square shapes: many Gram tiles per row range, long Q-form contractions
+    A = synth.make_matrix(m, n, kappa, seed=m + n)
+    with cq.Plan(m, n, precision=cq.CQR2_OZAKI_BF16) as p:
+        Q, R, info = p.factor(to_dev(A))
+    assert info.status == 0
+    _check(A, to_host(Q), to_host(R), kappa)
