@@ -52,10 +52,19 @@ WORKLOADS = {
 FP64_FMA_PER_CLK_PER_SM = 2
 GB300_SMS = 152
 
-# ncu DRAM bytes (read + write) per launch of the dominant kernel, keyed by
-# kernel name, workload and the SHA-256 of the source file it was measured
-# from; used only while that source is unchanged.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture (`profiles/`), keyed by kernel, workload and a hash of the kernel's
+# source file, so that an entry lapses (null) once the kernel changes. The
+# "tall" entries were captured on "mid" (2^20 of the 2^23 rows) and scaled by
+# the row count: these kernels stream their operands once per launch.
+NCU_TRAFFIC = {
+    "k_qform_gram_small@mid@32201450a5426255": 2145473280,
+    "k_qform_gram_small@tall@32201450a5426255": 17163786240,
+    "k_ozaki_gemm<7,QFORM>@mid@b5de47a1ccbfa09e": 2943822000,
+    "k_ozaki_gemm<7,QFORM>@tall@b5de47a1ccbfa09e": 23550576000,
+    "k_ozaki_gemm<7,GRAM>@mid@b5de47a1ccbfa09e": 3780151000,
+    "k_ozaki_gemm<7,GRAM>@tall@b5de47a1ccbfa09e": 30241208000,
+}
 
 
 def nominal_flops(m: int, n: int) -> float:
