@@ -4,8 +4,9 @@
 // This is not part of the paper; it serves the same Algorithm CQR2.
 //
 // Error-free split. With a shared exponent e along the contraction (per
-// column of X for the Gram, per row of X and per column of R^-1 for the
-// Q-form) every entry is rounded once to a fixed-point integer
+// column of X, for both products; for the Q-form X's column exponents are
+// folded into the rows of R^-1, which then has one exponent per column)
+// every entry is rounded once to a fixed-point integer
 //     x' = round(x * 2^(7 + 8(S-1) - e)),  |x'| <= 2^(7 + 8(S-1)),
 // and cut into S balanced base-256 digits, x = 2^e sum_s d_s 2^(-7-8s),
 // |d_0| <= 128, d_s in [-128, 127]. Every digit is exact in BF16. This is
@@ -23,12 +24,14 @@
 // FP64 with integer operations: correctly rounded for the Gram, within one
 // ulp for the Q-form (a shorter sequence; far below its truncation error).
 //
-// Kernel: persistent, one CTA per SM, 128 x 32 output tiles, BF16 operands
-// K-major in 128-byte swizzled shared memory, loaded by TMA (3-D maps over
-// [slice][row][k]). Warp 0 produces (TMA), warp 1 issues tcgen05.mma (M=128,
-// one MMA of N = 32 (S - s) per A slice s and K=16 step) into S group
-// accumulators of 32 TMEM columns, double buffered, and warps 2-9 drain them.
-// All waits are bounded; a timeout sets the status word and the CTA unwinds.
+// Kernel: persistent, one CTA per SM. BF16 operands in 128-byte swizzled
+// shared memory, loaded by TMA from the column slice planes [slice][column][m]
+// (the Q-form's X as an MN-major operand, everything else K-major). Warp 0
+// produces (TMA), warp 1 issues tcgen05.mma (M = 128, one MMA per A slice and
+// K = 16 step covering all its products), the other warps drain the group
+// accumulators. Gram: 128 x 64 tiles, one accumulator buffer; Q-form:
+// 128 x 32 tiles, two. All waits are bounded; a timeout sets the status word
+// and the CTA unwinds.
 #include <cuda.h>
 
 #include <algorithm>
