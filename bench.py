@@ -218,6 +218,16 @@ def run_oracle_sample(A_full: np.ndarray, budget_rows: int):
 
 # ------------------------------------------------------------- arms
 
+def workload_config(args, ws: int) -> dict:
+    """The bench line's config, the same for both arms."""
+    m, n, kappa, seed, desc = WORKLOADS[args.workload]
+    fused = args.variant == "fused" and args.precision == "fp64"
+    return {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
+            "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth,
+            "parallelism": f"replicas{ws}" if ws > 1 else "single",
+            "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"}
+
+
 def bench_reference(args, ws, rank):
     """The CPU FP64 oracle on the host cores (the reference arm)."""
     m, n, kappa, seed, desc = WORKLOADS[args.workload]
@@ -241,7 +251,7 @@ def bench_reference(args, ws, rank):
         "impl": "reference", "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": val, "unit": "TFLOP/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "m": rows, "n": n, "kappa": kappa, "sampled_rows": rows},
+        "config": dict(workload_config(args, ws), sampled_rows=rows),
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -367,10 +377,7 @@ def bench_ours(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-slices->f64",
         "data": "synthetic",
-        "config": {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
-                   "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth,
-                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"},
+        "config": workload_config(args, ws),
         "gpu_launches": launches,
         "roofline": roofline_of(per_stage, args.precision, fused, clk),
         "vs_fp64_peak": {"achieved": value / ws, "peak": fp64_peak, "frac": value / ws / fp64_peak},
