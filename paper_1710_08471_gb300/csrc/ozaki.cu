@@ -25,7 +25,8 @@
 // ulp for the Q-form (a shorter sequence; far below its truncation error).
 //
 // Kernel: persistent, one CTA per SM. BF16 operands in 128-byte swizzled
-// shared memory, loaded by TMA from the column slice planes [slice][column][m]
+// shared memory, loaded by TMA from the column slice planes, stored K-block
+// tiled as [slice][m / 64][column][m % 64] so that every box is contiguous
 // (the Q-form's X as an MN-major operand, everything else K-major). Warp 0
 // produces (TMA), warp 1 issues tcgen05.mma (M = 128, one MMA per A slice and
 // K = 16 step covering all its products), the other warps drain the group
@@ -179,7 +180,9 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ X
     double x[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) x[q] = k + q < m ? col[k + q] : 0.0;
-    write_digits4<S>(x, ee, planes + (size_t)j * mp + k, stride);
+    // K-block tiled: [slice][k / 64][column][k % 64], so that a TMA box of
+    // columns x 64 rows is one contiguous run of memory
+    write_digits4<S>(x, ee, planes + (size_t)(k >> 6) * ((size_t)n * 64) + (size_t)j * 64 + (k & 63), stride);
   }
 }
 
@@ -264,6 +267,14 @@ __device__ __forceinline__ void report_timeout(DevStatus* st) {
     __threadfence();
     st->status = 5;
   }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
   asm volatile(
@@ -535,17 +546,22 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           if (bwrapped && !(ok = mbar_wait(&bempty[buf], bph ^ 1u, p.st))) break;
           mbar_expect_tx(&bfull[buf], S * B_BYTES);
 #pragma unroll
-          for (int t = 0; t < S; ++t)
-            tma_load_3d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], k0, (int)w.j0, t);
+          for (int t = 0; t < S; ++t) {
+            if (MODE == OZ_GRAM)  // column slices, K-block tiled: (k % 64, column, k / 64, slice)
+              tma_load_4d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], 0, (int)w.j0, k0 >> 6, t);
+            else  // R^-1 slices [slice][column][k]
+              tma_load_3d(sB + (buf * S + t) * B_BYTES, &tB, &bfull[buf], k0, (int)w.j0, t);
+          }
 #pragma unroll
           for (int s = 0; s < S; ++s) {
             if (awrapped && !(ok = mbar_wait(&aempty[slot], aph ^ 1u, p.st))) break;
             mbar_expect_tx(&afull[slot], A_BYTES);
             if (MODE == OZ_GRAM) {
-              tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], k0, (int)w.i0, s);
-            } else {  // X read from its column slices: two 64-row boxes, m innermost
-              tma_load_3d(sA + slot * A_BYTES, &tA, &afull[slot], (int)w.i0, k0, s);
-              tma_load_3d(sA + slot * A_BYTES + A_BYTES / 2, &tA, &afull[slot], (int)w.i0 + OZ_BM / 2, k0, s);
+              tma_load_4d(sA + slot * A_BYTES, &tA, &afull[slot], 0, (int)w.i0, k0 >> 6, s);
+            } else {  // X from its column slices: two boxes of 64 rows (m) x 64 columns (k)
+              const int kb = (int)(w.i0 >> 6);
+              tma_load_4d(sA + slot * A_BYTES, &tA, &afull[slot], 0, k0, kb, s);
+              tma_load_4d(sA + slot * A_BYTES + A_BYTES / 2, &tA, &afull[slot], 0, k0, kb + 1, s);
             }
             if (++slot == NA) {
               slot = 0;
@@ -809,10 +825,19 @@ cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
+  // column slices, K-block tiled: dims (k % 64, column, k / 64, slice)
+  auto make_tiled = [&](CUtensorMap* map, uint32_t box_cols) -> bool {
+    cuuint64_t dims[4] = {(cuuint64_t)OZ_BK, (cuuint64_t)n, (cuuint64_t)(g.mp / OZ_BK), (cuuint64_t)S};
+    cuuint64_t strides[3] = {(cuuint64_t)OZ_BK * 2, (cuuint64_t)n * OZ_BK * 2, (cuuint64_t)n * g.mp * 2};
+    cuuint32_t box[4] = {(cuuint32_t)OZ_BK, box_cols, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
   static_assert(sizeof(CUtensorMap) <= sizeof(OzMaps::col_a), "tensor map storage");
-  bool ok = make((CUtensorMap*)maps.col_a, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BM) &&
-            make((CUtensorMap*)maps.col_b, planes, (uint64_t)g.mp, (uint64_t)n, OZ_GRAM_BN) &&
-            make((CUtensorMap*)maps.col_a_mn, planes, (uint64_t)g.mp, (uint64_t)n, OZ_BK) &&
+  bool ok = make_tiled((CUtensorMap*)maps.col_a, OZ_BM) && make_tiled((CUtensorMap*)maps.col_b, OZ_GRAM_BN) &&
+            make_tiled((CUtensorMap*)maps.col_a_mn, OZ_BK) &&
             make((CUtensorMap*)maps.rinv_b, rinv_planes, (uint64_t)g.np, (uint64_t)n, OZ_QFORM_BN);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
