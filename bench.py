@@ -60,10 +60,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@22cddf3ff476de44": 2943822000,
-    "k_ozaki_gemm<7,QFORM>@tall@22cddf3ff476de44": 23550576000,
-    "k_ozaki_gemm<7,GRAM>@mid@22cddf3ff476de44": 3780151000,
-    "k_ozaki_gemm<7,GRAM>@tall@22cddf3ff476de44": 30241208000,
+    "k_ozaki_gemm<7,QFORM>@mid@34ab8c0409c24419": 2942047000,
+    "k_ozaki_gemm<7,QFORM>@tall@34ab8c0409c24419": 23536376000,
+    "k_ozaki_gemm<7,GRAM>@mid@34ab8c0409c24419": 3773994000,
+    "k_ozaki_gemm<7,GRAM>@tall@34ab8c0409c24419": 30191952000,
 }
 
 
