@@ -60,10 +60,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@34ab8c0409c24419": 2942047000,
-    "k_ozaki_gemm<7,QFORM>@tall@34ab8c0409c24419": 23536376000,
-    "k_ozaki_gemm<7,GRAM>@mid@34ab8c0409c24419": 3773994000,
-    "k_ozaki_gemm<7,GRAM>@tall@34ab8c0409c24419": 30191952000,
+    "k_ozaki_gemm<7,QFORM>@mid@9c7a7ef2f997be24": 2942047000,
+    "k_ozaki_gemm<7,QFORM>@tall@9c7a7ef2f997be24": 23536376000,
+    "k_ozaki_gemm<7,GRAM>@mid@9c7a7ef2f997be24": 3773994000,
+    "k_ozaki_gemm<7,GRAM>@tall@9c7a7ef2f997be24": 30191952000,
 }
 
 

@@ -160,6 +160,17 @@ cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t plan, int32_t fused);
  * has a call in flight. */
 cqr2_status_t cqr2_plan_set_inverse_depth(cqr2_plan_t plan, int32_t depth);
 
+/* Self-test of the bounded-wait timeout path (no counterpart in the paper):
+ * runs one thread that waits, with the library's bounded mbarrier wait, on a
+ * barrier that nothing arrives at, for at most `polls` polls (1..2^24), and
+ * reports through a device status word exactly as the split-precision GEMM
+ * does when one of its waits runs out. Returns CQR2_ERR_TIMEOUT when the wait
+ * ran out (the expected outcome), CQR2_OK if it did not,
+ * CQR2_ERR_INVALID_ARG for polls outside the range, CQR2_ERR_CUDA or
+ * CQR2_ERR_OOM on a CUDA failure. Synchronises `stream` (may be NULL). The
+ * CUDA context stays usable afterwards. */
+cqr2_status_t cqr2_selftest_wait_timeout(int64_t polls, void* stream);
+
 /* Synchronize the plan's stream and report the outcome of the last
  * factorization enqueued on the plan. */
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info);

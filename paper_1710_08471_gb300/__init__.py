@@ -19,6 +19,7 @@ from ._native import (  # noqa: F401
     CQR2_ERR_INVALID_ARG,
     CQR2_ERR_NOT_SPD,
     CQR2_ERR_OOM,
+    CQR2_ERR_TIMEOUT,
     CQR2_ERR_UNSUPPORTED,
     CQR2_FP64,
     CQR2_FUSED,

@@ -67,6 +67,7 @@ SIGNATURES = {
     "cqr2_plan_set_gram_ctas": (C.c_int, [_P, C.c_int32]),
     "cqr2_plan_set_fused": (C.c_int, [_P, C.c_int32]),
     "cqr2_plan_set_inverse_depth": (C.c_int, [_P, C.c_int32]),
+    "cqr2_selftest_wait_timeout": (C.c_int, [C.c_int64, _P]),
     "cqr2_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(BatchConfig), _P]),
     "cqr2_batch_factor": (C.c_int, [_P, C.POINTER(Problem), C.c_int32, C.POINTER(Info)]),
     "cqr2_batch_destroy": (None, [_P]),

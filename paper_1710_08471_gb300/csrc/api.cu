@@ -677,6 +677,26 @@ cqr2_status_t cqr2_plan_set_inverse_depth(cqr2_plan_t p, int32_t depth) {
   return CQR2_OK;
 }
 
+cqr2_status_t cqr2_selftest_wait_timeout(int64_t polls, void* stream) {
+  if (polls < 1 || polls > (int64_t(1) << 24)) return CQR2_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevStatus* st = nullptr;
+  if (cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return CQR2_ERR_OOM;
+  }
+  DevStatus h{};
+  cqr2_status_t r = CQR2_OK;
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess || ozaki_selftest_wait(polls, st, s) != cudaSuccess ||
+      cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    r = CQR2_ERR_CUDA;
+  else if (h.status == 5)
+    r = CQR2_ERR_TIMEOUT;
+  cudaFree(st);
+  return r;
+}
+
 cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t p, int32_t fused) {
   if (!p) return CQR2_ERR_INVALID_ARG;
   p->fused = fused && !p->oz_S && qform_gram_fusable((int)p->n) && p->small;

@@ -131,6 +131,9 @@ cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool fr
 // partial holds max_splits n x n blocks; a geometry needing more is refused.
 cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
                        int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s);
+// One thread waits on an mbarrier nothing arrives at (bounded, `polls`
+// polls) and records a timeout in *st, as the split-precision GEMM does.
+cudaError_t ozaki_selftest_wait(long long polls, DevStatus* st, cudaStream_t s);
 // Q = X R^-1 from X's column slices (the Gram's planes) and R^-1's slices.
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
                         DevStatus* st, cudaStream_t s);

@@ -258,6 +258,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t phase, const Dev
   return false;
 }
 
+// Bounded wait that ignores the status word: after a timeout, the unwinding
+// CTA still waits (up to the limit) for its own copies and MMAs in flight.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* b, uint32_t phase) {
+  const uint32_t addr = smem_u32(b);
+  for (long long i = 0; i < (1ll << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // Records a timeout (status 5) in the status word; the first reporter wins.
 __device__ __forceinline__ void report_timeout(DevStatus* st) {
   if (atomicCAS(&st->lock, 0, 1) == 0) {
@@ -340,7 +356,7 @@ struct OzCfg {
                                 : 8;                              // A ring slots
   static constexpr int CPT = BN * 4 * NGRP / EPI;                 // columns per epilogue thread
   static constexpr int TMAX = 256 / BN;                           // products per MMA (N <= 256)
-  static constexpr int NBAR = 2 * NA + 4 + 2 * NBUF * S;
+  static constexpr int NBAR = 2 * NA + 4 + 2 * NBUF * S + 1;  // + the drain barrier
   static constexpr size_t SMEM = 1024 + (size_t)NA * A_BYTES + (size_t)2 * S * B_BYTES + 8 * NBAR + 16;
   static_assert(NBUF * S * BN <= 512, "accumulators must fit in TMEM");
   static_assert(CPT == 8 || CPT == 16 || CPT == 32, "epilogue load width");
@@ -498,7 +514,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
   uint64_t* bempty = bfull + 2;
   uint64_t* accfull = bempty + 2;       // [NBUF][S]
   uint64_t* accempty = accfull + NBUF * S;
-  uint32_t* tmem_slot = (uint32_t*)(accempty + NBUF * S);
+  uint64_t* drainbar = accempty + NBUF * S;  // MMA completion on the timeout path
+  uint32_t* tmem_slot = (uint32_t*)(drainbar + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -515,6 +532,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       mbar_init(&accfull[i], 1);
       mbar_init(&accempty[i], EPI / NGRP);  // one group drains a chunk
     }
+    mbar_init(drainbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -539,12 +557,16 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       int slot = 0, buf = 0;
       uint32_t aph = 0, bph = 0;
       bool awrapped = false, bwrapped = false;  // ring slots used once already
+      int alast[NA], blast[2];                   // parity of each slot's last fill (-1: none)
+      for (int i = 0; i < NA; ++i) alast[i] = -1;
+      blast[0] = blast[1] = -1;
       for (int64_t it = it_begin; it < it_end && ok; ++it) {
         const OzItem w = oz_item<MODE, BN>(p, it);
         for (int kb = 0; kb < w.nk; ++kb) {
           const int k0 = (int)(w.kbase + (int64_t)kb * OZ_BK);
           if (bwrapped && !(ok = mbar_wait(&bempty[buf], bph ^ 1u, p.st))) break;
           mbar_expect_tx(&bfull[buf], S * B_BYTES);
+          blast[buf] = (int)bph;
 #pragma unroll
           for (int t = 0; t < S; ++t) {
             if (MODE == OZ_GRAM)  // column slices, K-block tiled: (k % 64, column, k / 64, slice)
@@ -556,6 +578,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           for (int s = 0; s < S; ++s) {
             if (awrapped && !(ok = mbar_wait(&aempty[slot], aph ^ 1u, p.st))) break;
             mbar_expect_tx(&afull[slot], A_BYTES);
+            alast[slot] = (int)aph;
             if (MODE == OZ_GRAM) {
               tma_load_4d(sA + slot * A_BYTES, &tA, &afull[slot], 0, (int)w.i0, k0 >> 6, s);
             } else {  // X from its column slices: two boxes of 64 rows (m) x 64 columns (k)
@@ -576,7 +599,14 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           }
         }
       }
-      if (!ok) report_timeout(p.st);
+      if (!ok) {
+        report_timeout(p.st);
+        // wait for the copies still in flight: the last issued fill of every slot
+        for (int i = 0; i < NA; ++i)
+          if (alast[i] >= 0) mbar_wait_drain(&afull[i], (uint32_t)alast[i]);
+        for (int i = 0; i < 2; ++i)
+          if (blast[i] >= 0) mbar_wait_drain(&bfull[i], (uint32_t)blast[i]);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -650,7 +680,11 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
           }
         }
       }
-      if (!ok) report_timeout(p.st);
+      if (!ok) {
+        report_timeout(p.st);
+        mma_commit(drainbar);  // arrives once every MMA issued so far has completed
+        mbar_wait_drain(drainbar, 0);
+      }
     }
   } else {
     const int ew = warp - 2;                            // epilogue warp
@@ -723,6 +757,29 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
   }
 }
 
+// Self-test of the timeout path: one thread waits, with the GEMM's bounded
+// wait and a short limit, on an mbarrier that nothing arrives at; it then
+// reports the timeout and drains exactly as the GEMM's roles do. No memory is
+// touched but the status word.
+__global__ void k_selftest_wait(long long polls, DevStatus* st) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const uint32_t addr = smem_u32(&bar);
+  bool ok = false;
+  for (long long i = 0; i < polls && !ok; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(0u)
+        : "memory");
+    ok = done != 0;
+  }
+  if (!ok) report_timeout(st);
+}
+
 // Sum the split partials of the computed Gram tiles and mirror.
 __global__ void k_oz_gram_reduce(const double* __restrict__ partial, int nsplit, int n, double* __restrict__ W,
                                  int64_t ldw) {
@@ -774,6 +831,12 @@ int64_t sm_count_oz() {
 }
 
 // ------------------------------------------------------------ public (internal) API
+
+cudaError_t ozaki_selftest_wait(long long polls, DevStatus* st, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(polls, st);
+  count_launch();
+  return cudaGetLastError();
+}
 
 bool ozaki_supported(int n, int S) { return n >= 1 && n <= OZAKI_MAX_N && S >= 6 && S <= 7; }
 
