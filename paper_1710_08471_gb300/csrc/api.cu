@@ -24,6 +24,7 @@ struct cqr2_plan_st {
   int64_t gram_cap = 0;  // row ranges the Gram partials have room for (any cm <= m)
   int inv_depth = 0;         // CholInv levels without Y21 (0: whole inverse)
   double* Tsolve = nullptr;  // block-substitution scratch, ldt x right_solve_temp_cols(n)
+  double* skws = nullptr;    // split-k scratch of CholInv's small products
   int64_t ldt = 0;
   int64_t oz_cap = 0;    // same for the split-precision Gram partials
   int precision = CQR2_FP64;
@@ -171,8 +172,8 @@ cudaError_t plan_cholinv(cqr2_plan_st* p, int pass, cudaStream_t s) {
   const int n = (int)p->n;
   if (p->inv_depth > 0)
     return cholinv_depth(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->Tsolve, p->ldt, p->st, pass, p->inv_depth,
-                         s);
-  return cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s);
+                         s, p->skws, cholinv_splitk_doubles());
+  return cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s, p->skws, cholinv_splitk_doubles());
 }
 
 // X = B R^-1 = B L^-T (general path, rows x n): one triangular multiply by
@@ -241,7 +242,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
-      TRY(cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass_base + pass, s));
+      TRY(plan_cholinv(p, pass_base + pass, s));
       if (pass == 1) TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
     }
     {
@@ -505,6 +506,8 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
     take((size_t)n * sizeof(int));                                   // 19 R^-1 exponents
     take((size_t)p->oz_cap * n * n * sizeof(double));                // 20 Gram partials
   }
+  const int i_sk = k;
+  take(cholinv_splitk_doubles() * sizeof(double));                   // split-k scratch of CholInv
   if (cudaMalloc(&p->ws, sz) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -532,6 +535,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   p->Q1 = p->small ? nullptr : at(9);
   p->lspart = at(10);
   p->st = reinterpret_cast<DevStatus*>(p->ws + off[11]);
+  p->skws = at(i_sk);
   if (oz_S) {
     p->oz_planes = reinterpret_cast<unsigned short*>(p->ws + off[14]);
     p->oz_rinv = reinterpret_cast<unsigned short*>(p->ws + off[15]);
@@ -766,7 +770,8 @@ cqr2_status_t cqr2_cholinv(cqr2_plan_t p, const double* dW, int64_t ldw, double*
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
   TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), p->stream));
-  TRY(cholinv((int)p->n, dW, ldw, dL, ldl, dY, ldy, p->Wk, p->U, p->st, 1, p->stream));
+  TRY(cholinv((int)p->n, dW, ldw, dL, ldl, dY, ldy, p->Wk, p->U, p->st, 1, p->stream, p->skws,
+              cholinv_splitk_doubles()));
   if (info) return read_info(p, info);
   return CQR2_OK;
 }

@@ -37,16 +37,21 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
     T[j * LD + i] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // Right-looking Cholesky.
+  // Right-looking Cholesky. GB300 runs about two FP64 operations per clock per
+  // SM, so each pivot's reciprocal is formed once (thread 0) and the column
+  // is scaled by multiplication; the reciprocals also scale the inverse below.
+  __shared__ double rdiag[NB];
   for (int k = 0; k < nb; ++k) {
     if (t == 0) {
       const double d = S[k * LD + k];
       if (!(d > 0.0) || !isfinite(d)) report_pivot(st, pass, off + k, d);
-      S[k * LD + k] = sqrt(d);
+      const double l = sqrt(d);
+      S[k * LD + k] = l;
+      rdiag[k] = 1.0 / l;
     }
     __syncthreads();
-    const double l = S[k * LD + k];
-    for (int i = k + 1 + t; i < nb; i += 256) S[k * LD + i] /= l;
+    const double rl = rdiag[k];
+    for (int i = k + 1 + t; i < nb; i += 256) S[k * LD + i] *= rl;
     __syncthreads();
     for (int j = k + 1 + tx; j < nb; j += 16)
       for (int i = j + ty; i < nb; i += 16) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
@@ -54,8 +59,8 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   }
   // Right-looking inverse: solve L Y = I one row of Y at a time.
   for (int k = 0; k < nb; ++k) {
-    const double lkk = S[k * LD + k];
-    for (int j = t; j <= k; j += 256) T[j * LD + k] /= lkk;
+    const double rkk = rdiag[k];
+    for (int j = t; j <= k; j += 256) T[j * LD + k] *= rkk;
     __syncthreads();
     for (int j = tx; j <= k; j += 16)
       for (int i = k + 1 + ty; i < nb; i += 16) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
@@ -94,7 +99,7 @@ __global__ void k_copy_upper(const double* __restrict__ X, int64_t ldx, int n, d
 constexpr size_t BASE_SMEM = 2 * NB * LD * sizeof(double);
 
 cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
-                int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s) {
+                int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s, double* ws, size_t wsn) {
   if (n <= NB) {
     k_cholinv_base<<<1, 256, BASE_SMEM, s>>>(Wk, ldk, n, L, ldl, Y, ldy, st, pass, off);
     count_launch();
@@ -104,49 +109,51 @@ cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* 
   const int n2 = n - n1;
   cudaError_t e;
   // [L11, Y11] = CholInv(W11)
-  if ((e = rec(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s)) != cudaSuccess) return e;
+  if ((e = rec(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s, ws, wsn)) != cudaSuccess) return e;
   // L21 = W21 Y11^T
   if ((e = gemm_f64(n2, n1, n1, 1.0, Wk + n1, ldk, Y, ldy, 0.0, L + n1, ldl, GEMM_TB | GEMM_B_UPPER | GEMM_BETA0,
-                    s)) != cudaSuccess)
+                    s, ws, wsn)) != cudaSuccess)
     return e;
   // W22 <- W22 - L21 L21^T (lower triangle)
   double* W22 = Wk + n1 + (int64_t)n1 * ldk;
-  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s)) !=
-      cudaSuccess)
+  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s, ws,
+                    wsn)) != cudaSuccess)
     return e;
   // [L22, Y22] = CholInv(W22 - L21 L21^T)
   double* L22 = L + n1 + (int64_t)n1 * ldl;
   double* Y22 = Y + n1 + (int64_t)n1 * ldy;
-  if ((e = rec(n2, W22, ldk, L22, ldl, Y22, ldy, U, ldu, st, pass, off + n1, s)) != cudaSuccess) return e;
+  if ((e = rec(n2, W22, ldk, L22, ldl, Y22, ldy, U, ldu, st, pass, off + n1, s, ws, wsn)) != cudaSuccess) return e;
   // U = L21 Y11
-  if ((e = gemm_f64(n2, n1, n1, 1.0, L + n1, ldl, Y, ldy, 0.0, U, ldu, GEMM_B_LOWER | GEMM_BETA0, s)) != cudaSuccess)
+  if ((e = gemm_f64(n2, n1, n1, 1.0, L + n1, ldl, Y, ldy, 0.0, U, ldu, GEMM_B_LOWER | GEMM_BETA0, s, ws, wsn)) !=
+      cudaSuccess)
     return e;
   // Y21 = -Y22 U
-  return gemm_f64(n2, n1, n2, -1.0, Y22, ldy, U, ldu, 0.0, Y + n1, ldy, GEMM_A_LOWER | GEMM_BETA0, s);
+  return gemm_f64(n2, n1, n2, -1.0, Y22, ldy, U, ldu, 0.0, Y + n1, ldy, GEMM_A_LOWER | GEMM_BETA0, s, ws, wsn);
 }
 
 // Depth-limited recursion: the top `depth` levels form L21 by block forward
 // substitution through the diagonal blocks' inverses and leave Y21 zero.
 cudaError_t rec_depth(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
                       int64_t ldu, double* T, int64_t ldt, DevStatus* st, int pass, long long off, int depth,
-                      cudaStream_t s) {
-  if (depth <= 0 || n <= NB) return rec(n, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s);
+                      cudaStream_t s, double* ws, size_t wsn) {
+  if (depth <= 0 || n <= NB) return rec(n, Wk, ldk, L, ldl, Y, ldy, U, ldu, st, pass, off, s, ws, wsn);
   const int n1 = NB * (int)ceil_div(n, 2 * NB);
   const int n2 = n - n1;
   cudaError_t e;
   // [L11, Y11] with Y11 known on its leaf blocks only
-  if ((e = rec_depth(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, T, ldt, st, pass, off, depth - 1, s)) != cudaSuccess)
+  if ((e = rec_depth(n1, Wk, ldk, L, ldl, Y, ldy, U, ldu, T, ldt, st, pass, off, depth - 1, s, ws, wsn)) !=
+      cudaSuccess)
     return e;
   // L21 = W21 L11^-T
   if ((e = right_solve(n2, n1, Wk + n1, ldk, L + n1, ldl, L, ldl, Y, ldy, depth - 1, T, ldt, s)) != cudaSuccess)
     return e;
   // W22 <- W22 - L21 L21^T (lower triangle)
   double* W22 = Wk + n1 + (int64_t)n1 * ldk;
-  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s)) !=
-      cudaSuccess)
+  if ((e = gemm_f64(n2, n2, n1, -1.0, L + n1, ldl, L + n1, ldl, 1.0, W22, ldk, GEMM_TB | GEMM_C_LOWER, s, ws,
+                    wsn)) != cudaSuccess)
     return e;
   return rec_depth(n2, W22, ldk, L + n1 + (int64_t)n1 * ldl, ldl, Y + n1 + (int64_t)n1 * ldy, ldy, U, ldu, T, ldt,
-                   st, pass, off + n1, depth - 1, s);
+                   st, pass, off + n1, depth - 1, s, ws, wsn);
 }
 
 }  // namespace
@@ -182,12 +189,17 @@ cudaError_t right_solve(int64_t M, int N, const double* B, int64_t ldb, double* 
                      depth - 1, T, ldt, s);
 }
 
+// Split-k partials of one product: ks * M * N with ks * tiles <= SMs, so 256
+// SMs' worth of 64 x 64 tiles is enough for any size (the GEMM lowers ks
+// further if the scratch is short).
+size_t cholinv_splitk_doubles() { return (size_t)256 * 64 * 64; }
+
 int right_solve_temp_cols(int n) { return n <= NB ? n : NB * (int)ceil_div(n, 2 * NB); }
 
 cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                           double* work, double* U, double* T, int64_t ldt, DevStatus* st, int pass, int depth,
-                          cudaStream_t s) {
-  if (depth <= 0) return cholinv(n, W, ldw, L, ldl, Y, ldy, work, U, st, pass, s);
+                          cudaStream_t s, double* ws, size_t wsn) {
+  if (depth <= 0) return cholinv(n, W, ldw, L, ldl, Y, ldy, work, U, st, pass, s, ws, wsn);
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_cholinv_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BASE_SMEM)) !=
       cudaSuccess)
@@ -201,11 +213,11 @@ cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_
   if ((e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
       cudaSuccess)
     return e;
-  return rec_depth(n, work, n, L, ldl, Y, ldy, U, n, T, ldt, st, pass, 0, depth, s);
+  return rec_depth(n, work, n, L, ldl, Y, ldy, U, n, T, ldt, st, pass, 0, depth, s, ws, wsn);
 }
 
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
-                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s) {
+                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s, double* ws, size_t wsn) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_cholinv_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BASE_SMEM)) !=
       cudaSuccess)
@@ -219,7 +231,7 @@ cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl,
   if ((e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
       cudaSuccess)
     return e;
-  return rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s);
+  return rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s, ws, wsn);
 }
 
 // Shift of the shifted CholeskyQR pass: W += s I with

@@ -22,7 +22,8 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K, double alpha,
                                                  const double* __restrict__ A, int64_t lda,
                                                  const double* __restrict__ B, int64_t ldb, double beta,
-                                                 double* __restrict__ C, int64_t ldc, unsigned flags) {
+                                                 double* __restrict__ C, int64_t ldc, unsigned flags, int ksplit,
+                                                 double* __restrict__ P) {
   __shared__ double As[2][BK][BM + 1];
   __shared__ double Bs[2][BK][BN + 1];
   const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K
 
   if ((flags & GEMM_C_LOWER) && j0 > i0 + BM - 1) return;
   if ((flags & GEMM_C_UPPER) && i0 > j0 + BN - 1) {
+    if (ksplit > 1) return;  // the reduction writes the zeros
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -45,6 +47,12 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K
   if (flags & GEMM_B_LOWER) kb = max(kb, j0);
   if (flags & GEMM_B_UPPER) ke = min(ke, j0 + BN);
   kb = (kb / BK) * BK;
+  if (ksplit > 1) {  // this CTA's share of the k range, in whole k-slices
+    const int64_t per = ((ke - kb + BK - 1) / BK + ksplit - 1) / ksplit * BK;
+    const int64_t z0 = kb + (int64_t)blockIdx.z * per;
+    ke = min(ke, z0 + per);
+    kb = z0;
+  }
 
   double acc[4][4];
 #pragma unroll
@@ -120,6 +128,17 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K
     }
   }
 
+  if (ksplit > 1) {  // partial of split z: P[z][j][i] = alpha * sum over its k range
+    double* Pz = P + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t gi = i0 + tx + 16 * r, gj = j0 + ty + 16 * c;
+        if (gi < M && gj < N) Pz[gi + gj * M] = alpha * acc[r][c];
+      }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -137,20 +156,59 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int64_t M, int64_t N, int64_t K
     }
 }
 
+// C = sum of the k-split partials in split order (deterministic), then beta C
+// and the output-triangle rules as in the unsplit kernel.
+__global__ void k_gemm_splitk_reduce(int64_t M, int64_t N, int ksplit, const double* __restrict__ P, double beta,
+                                     double* __restrict__ C, int64_t ldc, unsigned flags) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  const int64_t gi = e % M, gj = e / M;
+  if ((flags & GEMM_C_LOWER) && gi < gj) return;
+  if ((flags & GEMM_C_UPPER) && gi > gj) {
+    C[gi + gj * ldc] = 0.0;
+    return;
+  }
+  double v = 0.0;
+  for (int z = 0; z < ksplit; ++z) v += P[(int64_t)z * M * N + e];
+  if (!(flags & GEMM_BETA0)) v = fma(beta, C[gi + gj * ldc], v);
+  C[gi + gj * ldc] = v;
+}
+
 }  // namespace
 
 cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
-                     int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags, cudaStream_t s) {
+                     int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags, cudaStream_t s, double* ws,
+                     size_t ws_doubles) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int64_t gx = ceil_div(M, BM), gy = ceil_div(N, BN);
   if (gy > 65535) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)gx, (unsigned)gy);
+  // Small products fill few SMs, each doing about 2 FP64 FMA per clock: with
+  // scratch, split k over up to 8 CTAs per tile (whole k-slices each).
+  int ks = 1;
+  if (ws && K >= 2 * BK) {
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = std::max<int64_t>(1, sms / (gx * gy));
+    ks = (int)std::min<int64_t>({want, 8, K / BK});
+    while (ks > 1 && (size_t)ks * M * N > ws_doubles) --ks;
+  }
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
   const bool ta = flags & GEMM_TA, tb = flags & GEMM_TB;
-  if (!ta && !tb) k_gemm_f64<false, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
-  else if (!ta && tb) k_gemm_f64<false, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
-  else if (ta && !tb) k_gemm_f64<true, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
-  else k_gemm_f64<true, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags);
+  if (!ta && !tb)
+    k_gemm_f64<false, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, ks, ws);
+  else if (!ta && tb)
+    k_gemm_f64<false, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, ks, ws);
+  else if (ta && !tb)
+    k_gemm_f64<true, false><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, ks, ws);
+  else
+    k_gemm_f64<true, true><<<grid, NT, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, ks, ws);
   count_launch();
+  if (ks > 1) {
+    const int64_t total = M * N;
+    k_gemm_splitk_reduce<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(M, N, ks, ws, beta, C, ldc, flags);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

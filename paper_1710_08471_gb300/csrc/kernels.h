@@ -66,23 +66,30 @@ enum : unsigned {
   GEMM_C_UPPER = 1u << 7,   // only C(i,j), i <= j, is computed; i > j written as 0
   GEMM_BETA0 = 1u << 8,     // C is not read (beta = 0)
 };
+// With scratch ws (ws_doubles doubles), a product too small to fill the GPU
+// splits k over up to 8 CTAs per tile and sums the partials in a fixed order
+// (deterministic; ws must not alias A, B or C).
 cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                      const double* B, int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags,
-                     cudaStream_t s);
+                     cudaStream_t s, double* ws = nullptr, size_t ws_doubles = 0);
 
 // ---------------------------------------------------------------- CholInv
 // [L, Y] = CholInv(W) (Algorithm 1): recursive halving with FP64 GEMMs and a
 // one-CTA base case of size <= 64. `work` and `U` are n x n scratch (ld n).
 constexpr int CHOLINV_BASE = 64;
+// ws (wsn doubles, may be null) is split-k scratch for the recursion's small
+// products; cholinv_splitk_doubles() is enough for any n.
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
-                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s);
+                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s, double* ws = nullptr,
+                    size_t wsn = 0);
+size_t cholinv_splitk_doubles();
 // Inverse depth (the paper's triangular inverted blocks): the top `depth`
 // halvings form L21 = W21 L11^-T by block forward substitution and leave Y21
 // zero, so Y holds the inverses of L's diagonal blocks only. T is scratch of
 // n x right_solve_temp_cols(n) doubles (ld ldt >= n).
 cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                           double* work, double* U, double* T, int64_t ldt, DevStatus* st, int pass, int depth,
-                          cudaStream_t s);
+                          cudaStream_t s, double* ws = nullptr, size_t wsn = 0);
 // X = B L^-T (M x N) for lower-triangular L whose diagonal-block inverses of a
 // depth-`depth` halving are in Y: X1 = B1 L11^-T, X2 = (B2 - X1 L21^T) L22^-T.
 // X may equal B. T is scratch of M x right_solve_temp_cols(N) (ld ldt >= M).
