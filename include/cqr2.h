@@ -203,7 +203,10 @@ cqr2_status_t cqr2_trmm_upper(cqr2_plan_t plan, const double* dR2, int64_t ld2, 
 /* ---- Many independent factorizations ---- */
 
 /* One problem of a batch: A (m x n, lda) is factored into Q (m x n, ldq) and
- * R (n x n, ldr), all device pointers, m >= n >= 1, Q not aliasing A. */
+ * R (n x n, ldr), all device pointers, m >= n >= 1, Q not aliasing A.
+ * b and x are both NULL (a factorization) or both set (least squares: x, n
+ * entries, minimizes ||A x - b|| for b, m entries, by R x = Q^T b, as
+ * cqr2_lstsq does). */
 typedef struct {
   int64_t m, n;
   const double* A;
@@ -212,6 +215,8 @@ typedef struct {
   int64_t ldq;
   double* R;
   int64_t ldr;
+  const double* b;
+  double* x;
 } cqr2_problem_t;
 
 typedef struct cqr2_batch_st* cqr2_batch_t;
@@ -236,13 +241,23 @@ typedef struct {
 cqr2_status_t cqr2_batch_create(cqr2_batch_t* batch, int32_t max_count, int32_t precision,
                                 const cqr2_batch_config_t* cfg, void* stream);
 
-/* Factor `count` problems (host array of descriptors). All work is enqueued
- * on the batch's stream (and streams joined back into it). With infos (a host
- * array of count entries) the call synchronizes and reports every problem's
- * outcome, returning CQR2_ERR_NOT_SPD if any broke down; with NULL it is
- * asynchronous. */
+/* Factor (or solve, where b is given) `count` problems (host array of
+ * descriptors). All work is enqueued on the batch's stream (and streams
+ * joined back into it). With infos (a host array of count entries) the call
+ * synchronizes and reports every problem's outcome, returning
+ * CQR2_ERR_NOT_SPD if any broke down; with NULL it is asynchronous and
+ * cqr2_batch_info reports the outcomes later. A call first waits until the
+ * batch's previous call has finished on the device (its descriptors and
+ * status words are reused). A problem's result depends only on the problem
+ * and the batch's configuration, not on the rest of the batch: the route
+ * (grouped kernel or plan) is chosen from m and n alone. */
 cqr2_status_t cqr2_batch_factor(cqr2_batch_t batch, const cqr2_problem_t* problems, int32_t count,
                                 cqr2_info_t* infos);
+
+/* Outcomes of the batch's last cqr2_batch_factor call (count must equal that
+ * call's count): waits for the batch's stream, then fills infos as the
+ * synchronous form does and returns the same status. */
+cqr2_status_t cqr2_batch_info(cqr2_batch_t batch, int32_t count, cqr2_info_t* infos);
 
 void cqr2_batch_destroy(cqr2_batch_t batch);
 

@@ -284,21 +284,37 @@ class Batch:
         self.max_count = int(max_count)
 
     def factor(self, problems, sync: bool = True):
-        """problems: list of (A, Q, R) column-major CUDA float64 tensors.
-        Returns a list of Info (sync=True) or None."""
+        """problems: list of (A, Q, R) or, for least squares, (A, Q, R, b, x)
+        with column-major CUDA float64 matrices and contiguous vectors b (m)
+        and x (n). Returns a list of Info (sync=True) or None (then info()
+        reports the outcomes)."""
         k = len(problems)
         arr = (N.Problem * max(k, 1))()
-        for i, (A, Q, R) in enumerate(problems):
+        for i, pr in enumerate(problems):
+            A, Q, R = pr[0], pr[1], pr[2]
             m, n = A.shape
             a, lda = _mat(A, m, n, "A")
             q, ldq = _mat(Q, m, n, "Q")
             r, ldr = _mat(R, n, n, "R")
-            arr[i] = N.Problem(m, n, a, lda, q, ldq, r, ldr)
+            bp = xp = None
+            if len(pr) > 3:
+                bp, xp = _vec(pr[3], m, "b"), _vec(pr[4], n, "x")
+            arr[i] = N.Problem(m, n, a, lda, q, ldq, r, ldr, bp, xp)
         infos = (Info * max(k, 1))() if sync else None
         st = N.load().cqr2_batch_factor(self.handle, arr, k, infos)
+        self._last = k
         if st not in (CQR2_OK, CQR2_ERR_NOT_SPD):
             N.check(st, "cqr2_batch_factor")
         return list(infos)[:k] if sync else None
+
+    def info(self):
+        """Outcomes of the last factor() call (waits for it)."""
+        k = getattr(self, "_last", 0)
+        infos = (Info * max(k, 1))()
+        st = N.load().cqr2_batch_info(self.handle, k, infos)
+        if st not in (CQR2_OK, CQR2_ERR_NOT_SPD, N.CQR2_ERR_TIMEOUT):
+            N.check(st, "cqr2_batch_info")
+        return list(infos)[:k]
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -36,7 +36,7 @@ class Info(C.Structure):
 class Problem(C.Structure):
     """cqr2_problem_t"""
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64), ("Q", C.c_void_p),
-                ("ldq", C.c_int64), ("R", C.c_void_p), ("ldr", C.c_int64)]
+                ("ldq", C.c_int64), ("R", C.c_void_p), ("ldr", C.c_int64), ("b", C.c_void_p), ("x", C.c_void_p)]
 
 
 class BatchConfig(C.Structure):
@@ -70,6 +70,7 @@ SIGNATURES = {
     "cqr2_selftest_wait_timeout": (C.c_int, [C.c_int64, _P]),
     "cqr2_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(BatchConfig), _P]),
     "cqr2_batch_factor": (C.c_int, [_P, C.POINTER(Problem), C.c_int32, C.POINTER(Info)]),
+    "cqr2_batch_info": (C.c_int, [_P, C.c_int32, C.POINTER(Info)]),
     "cqr2_batch_destroy": (None, [_P]),
     "cqr2_autotune": (C.c_int, [_I64, _I64, C.c_int32, C.POINTER(TuneResult)]),
     "cqr2_tune_set_small_limit": (C.c_int, [_I64]),

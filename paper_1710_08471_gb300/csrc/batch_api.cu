@@ -45,6 +45,12 @@ struct cqr2_batch_st {
     int64_t m_max = 0;
   };
   std::map<std::pair<int64_t, int>, PlanSlot> plans;  // (n, side stream) -> plan
+  // the last call: its end on the batch stream and where each outcome lives
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  int32_t last_count = 0;
+  std::vector<int> last_small;                 // problem index per grouped job
+  std::vector<int> last_used;                  // problem index per planned status word
 };
 
 namespace {
@@ -73,6 +79,83 @@ bool lookup_tune(int64_t m, int64_t n, int precision, TuneEntry* e) {
   if (it == g_tune.end()) return false;
   *e = it->second;
   return true;
+}
+
+// Enqueue one batch call on b's stream: routing, the grouped launch, the
+// planned problems on side streams, and the copies of every outcome to the
+// host. Records where each outcome lives in b->last_small / b->last_used.
+cqr2_status_t batch_enqueue(cqr2_batch_t b, const cqr2_problem_t* problems, int32_t count) {
+  // route by shape alone
+  std::vector<int> small, large;
+  for (int i = 0; i < count; ++i) {
+    const cqr2_problem_t& q = problems[i];
+    const bool is_small = q.n <= BATCH_SMALL_MAX_N && (double)q.m * q.n * q.n <= (double)b->cfg.small_work_limit;
+    (is_small ? small : large).push_back(i);
+  }
+  std::sort(small.begin(), small.end(), [&](int a, int c) {
+    return (double)problems[a].m * problems[a].n * problems[a].n > (double)problems[c].m * problems[c].n * problems[c].n;
+  });
+  // grouped launch for the small problems (on the batch stream)
+  if (!small.empty()) {
+    for (size_t k = 0; k < small.size(); ++k) {
+      const cqr2_problem_t& q = problems[small[k]];
+      b->h_probs[k] = BatchProblem{q.m, q.n, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr, q.b, q.x};
+    }
+    if (cudaMemcpyAsync(b->d_probs, b->h_probs, sizeof(BatchProblem) * small.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+    if (cqr2_small_batched(b->d_probs, (int)small.size(), b->d_next, b->d_status, b->stream) != cudaSuccess)
+      return CQR2_ERR_CUDA;
+  }
+  b->last_small = small;
+  // the others: plans on side streams forked from the batch stream
+  if (!large.empty()) {
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+    const int ns = (int)std::min<size_t>(b->side.size(), large.size());
+    for (int s = 0; s < ns; ++s)
+      if (cudaStreamWaitEvent(b->side[s], b->fork, 0) != cudaSuccess) return CQR2_ERR_CUDA;
+    for (size_t k = 0; k < large.size(); ++k) {
+      const cqr2_problem_t& q = problems[large[k]];
+      const int s = (int)(k % ns);
+      auto& slot = b->plans[{q.n, s}];
+      if (!slot.plan || slot.m_max < q.m) {
+        if (slot.plan) {
+          cudaStreamSynchronize(b->side[s]);
+          cqr2_plan_destroy(slot.plan);
+          slot.plan = nullptr;
+        }
+        const int64_t mm = std::max<int64_t>(q.m, slot.m_max);
+        int prec = b->precision;
+        if (prec != CQR2_FP64 && q.n > OZAKI_MAX_N) prec = CQR2_FP64;
+        cqr2_status_t r = cqr2_plan_create(&slot.plan, mm, q.n, prec, b->cfg.fused ? CQR2_FUSED : 0, b->side[s]);
+        if (r != CQR2_OK) return r;
+        slot.m_max = mm;
+        TuneEntry te;
+        if (lookup_tune(q.m, q.n, prec, &te)) {
+          cqr2_plan_set_gram_ctas(slot.plan, te.gram_ctas);
+          cqr2_plan_set_fused(slot.plan, te.fused);
+        }
+      }
+      cqr2_status_t r = q.b ? cqr2_lstsq_rows(slot.plan, q.m, q.A, q.lda, q.b, q.x, q.Q, q.ldq, q.R, q.ldr, nullptr)
+                            : cqr2_factor_rows(slot.plan, q.m, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr, nullptr);
+      if (r != CQR2_OK) return r;
+      if (plan_status_copy(slot.plan, b->d_lstatus + b->last_used.size(), b->side[s]) != cudaSuccess)
+        return CQR2_ERR_CUDA;
+      b->last_used.push_back(large[k]);
+    }
+    for (int s = 0; s < ns; ++s) {
+      if (cudaEventRecord(b->joins[s], b->side[s]) != cudaSuccess) return CQR2_ERR_CUDA;
+      if (cudaStreamWaitEvent(b->stream, b->joins[s], 0) != cudaSuccess) return CQR2_ERR_CUDA;
+    }
+  }
+  // the outcomes travel to the host with the work, so cqr2_batch_info only waits
+  if (!small.empty() && cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * small.size(),
+                                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return CQR2_ERR_CUDA;
+  if (!b->last_used.empty() && cudaMemcpyAsync(b->h_lstatus, b->d_lstatus, sizeof(DevStatus) * b->last_used.size(),
+                                               cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return CQR2_ERR_CUDA;
+  return CQR2_OK;
 }
 
 }  // namespace
@@ -111,7 +194,8 @@ cqr2_status_t cqr2_batch_create(cqr2_batch_t* batch, int32_t max_count, int32_t 
             cudaMallocHost(&b->h_status, sizeof(BatchStatus) * max_count) == cudaSuccess &&
             cudaMalloc(&b->d_lstatus, sizeof(DevStatus) * max_count) == cudaSuccess &&
             cudaMallocHost(&b->h_lstatus, sizeof(DevStatus) * max_count) == cudaSuccess &&
-            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < b->cfg.streams; ++i) {
     cudaStream_t s;
     cudaEvent_t e;
@@ -138,6 +222,7 @@ void cqr2_batch_destroy(cqr2_batch_t b) {
   for (cudaStream_t s : b->side) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
   cudaFree(b->d_probs);
   cudaFree(b->d_status);
   cudaFree(b->d_next);
@@ -156,81 +241,36 @@ cqr2_status_t cqr2_batch_factor(cqr2_batch_t b, const cqr2_problem_t* problems, 
   for (int i = 0; i < count; ++i) {
     const cqr2_problem_t& q = problems[i];
     if (q.n < 1 || q.m < q.n || !q.A || !q.Q || !q.R || q.lda < q.m || q.ldq < q.m || q.ldr < q.n ||
-        (const void*)q.A == (const void*)q.Q)
+        (const void*)q.A == (const void*)q.Q || (q.b == nullptr) != (q.x == nullptr))
       return CQR2_ERR_INVALID_ARG;
   }
-  // route
-  std::vector<int> small, large;
-  for (int i = 0; i < count; ++i) {
-    const cqr2_problem_t& q = problems[i];
-    const bool is_small = q.n <= BATCH_SMALL_MAX_N && (double)q.m * q.n * q.n <= (double)b->cfg.small_work_limit;
-    (is_small ? small : large).push_back(i);
+  // the previous call's descriptors and status words are about to be reused
+  if (b->pending && cudaEventSynchronize(b->done) != cudaSuccess) return CQR2_ERR_CUDA;
+  b->pending = false;
+  b->last_count = 0;
+  b->last_small.clear();
+  b->last_used.clear();
+  // whatever gets enqueued, the next call waits for it
+  const cqr2_status_t r = batch_enqueue(b, problems, count);
+  const bool recorded = cudaEventRecord(b->done, b->stream) == cudaSuccess;
+  b->pending = recorded;
+  if (r != CQR2_OK || !recorded) {
+    b->last_small.clear();
+    b->last_used.clear();
+    return r != CQR2_OK ? r : CQR2_ERR_CUDA;
   }
-  std::sort(small.begin(), small.end(), [&](int a, int c) {
-    return (double)problems[a].m * problems[a].n * problems[a].n > (double)problems[c].m * problems[c].n * problems[c].n;
-  });
-  // grouped launch for the small problems (on the batch stream)
-  if (!small.empty()) {
-    for (size_t k = 0; k < small.size(); ++k) {
-      const cqr2_problem_t& q = problems[small[k]];
-      b->h_probs[k] = BatchProblem{q.m, q.n, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr};
-    }
-    if (cudaMemcpyAsync(b->d_probs, b->h_probs, sizeof(BatchProblem) * small.size(), cudaMemcpyHostToDevice,
-                        b->stream) != cudaSuccess)
-      return CQR2_ERR_CUDA;
-    if (cqr2_small_batched(b->d_probs, (int)small.size(), b->d_next, b->d_status, b->stream) != cudaSuccess)
-      return CQR2_ERR_CUDA;
-  }
-  // the others: plans on side streams forked from the batch stream
-  std::vector<std::pair<int, cqr2_plan_t>> used;
-  if (!large.empty()) {
-    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return CQR2_ERR_CUDA;
-    const int ns = (int)std::min<size_t>(b->side.size(), large.size());
-    for (int s = 0; s < ns; ++s)
-      if (cudaStreamWaitEvent(b->side[s], b->fork, 0) != cudaSuccess) return CQR2_ERR_CUDA;
-    for (size_t k = 0; k < large.size(); ++k) {
-      const cqr2_problem_t& q = problems[large[k]];
-      const int s = (int)(k % ns);
-      auto& slot = b->plans[{q.n, s}];
-      if (!slot.plan || slot.m_max < q.m) {
-        if (slot.plan) {
-          cudaStreamSynchronize(b->side[s]);
-          cqr2_plan_destroy(slot.plan);
-          slot.plan = nullptr;
-        }
-        const int64_t mm = std::max<int64_t>(q.m, slot.m_max);
-        int prec = b->precision;
-        if (prec != CQR2_FP64 && q.n > OZAKI_MAX_N) prec = CQR2_FP64;
-        cqr2_status_t r = cqr2_plan_create(&slot.plan, mm, q.n, prec, b->cfg.fused ? CQR2_FUSED : 0, b->side[s]);
-        if (r != CQR2_OK) return r;
-        slot.m_max = mm;
-        TuneEntry te;
-        if (lookup_tune(q.m, q.n, prec, &te)) {
-          cqr2_plan_set_gram_ctas(slot.plan, te.gram_ctas);
-          cqr2_plan_set_fused(slot.plan, te.fused);
-        }
-      }
-      cqr2_status_t r = cqr2_factor_rows(slot.plan, q.m, q.A, q.lda, q.Q, q.ldq, q.R, q.ldr, nullptr);
-      if (r != CQR2_OK) return r;
-      if (plan_status_copy(slot.plan, b->d_lstatus + used.size(), b->side[s]) != cudaSuccess) return CQR2_ERR_CUDA;
-      used.push_back({large[k], slot.plan});
-    }
-    for (int s = 0; s < ns; ++s) {
-      if (cudaEventRecord(b->joins[s], b->side[s]) != cudaSuccess) return CQR2_ERR_CUDA;
-      if (cudaStreamWaitEvent(b->stream, b->joins[s], 0) != cudaSuccess) return CQR2_ERR_CUDA;
-    }
-  }
+  b->last_count = count;
   if (!infos) return CQR2_OK;
-  // outcome per problem (synchronizes)
+  return cqr2_batch_info(b, count, infos);
+}
+
+cqr2_status_t cqr2_batch_info(cqr2_batch_t b, int32_t count, cqr2_info_t* infos) {
+  if (!b || !infos || count != b->last_count) return CQR2_ERR_INVALID_ARG;
+  if (b->pending && cudaEventSynchronize(b->done) != cudaSuccess) return CQR2_ERR_CUDA;
+  b->pending = false;
   cqr2_status_t worst = CQR2_OK;
-  if (!small.empty()) {
-    if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(BatchStatus) * small.size(), cudaMemcpyDeviceToHost,
-                        b->stream) != cudaSuccess)
-      return CQR2_ERR_CUDA;
-  }
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CQR2_ERR_CUDA;
-  for (size_t k = 0; k < small.size(); ++k) {
-    cqr2_info_t& in = infos[small[k]];
+  for (size_t k = 0; k < b->last_small.size(); ++k) {
+    cqr2_info_t& in = infos[b->last_small[k]];
     const BatchStatus& st = b->h_status[k];
     in.status = st.failed_pass ? CQR2_ERR_NOT_SPD : CQR2_OK;
     in.failed_pass = st.failed_pass;
@@ -238,14 +278,8 @@ cqr2_status_t cqr2_batch_factor(cqr2_batch_t b, const cqr2_problem_t* problems, 
     in.pivot_value = 0.0;
     if (st.failed_pass) worst = CQR2_ERR_NOT_SPD;
   }
-  // Each planned problem's status word was copied out right after its call.
-  if (!used.empty()) {
-    if (cudaMemcpy(b->h_lstatus, b->d_lstatus, sizeof(DevStatus) * used.size(), cudaMemcpyDeviceToHost) !=
-        cudaSuccess)
-      return CQR2_ERR_CUDA;
-  }
-  for (size_t k = 0; k < used.size(); ++k) {
-    cqr2_info_t& in = infos[used[k].first];
+  for (size_t k = 0; k < b->last_used.size(); ++k) {
+    cqr2_info_t& in = infos[b->last_used[k]];
     const DevStatus& st = b->h_lstatus[k];
     in.status = st.status == 0 ? CQR2_OK : (st.status == 5 ? CQR2_ERR_TIMEOUT : CQR2_ERR_NOT_SPD);
     in.failed_pass = st.status == 2 ? st.pass : 0;

@@ -7,7 +7,9 @@
 //   triangular inverse, the base case of Algorithm 1),
 //   Q1 = A Y1^T panel by panel, its Gram W2 accumulated on the fly (the fused
 //   pass-1 Q-form / pass-2 Gram), Q1 staged in the output Q,
-//   [L2, Y2] = CholInv(W2), Q = Q1 Y2^T in place, R = L2^T L1^T.
+//   [L2, Y2] = CholInv(W2), Q = Q1 Y2^T in place, R = L2^T L1^T,
+//   and, for a least-squares problem (b given), c = Q^T b accumulated while
+//   the final Q is formed and x from R x = c by back substitution (one warp).
 // One launch replaces the ~40 launches a planned factorization issues, which
 // dominate for small m n^2. A breakdown is recorded per problem (pass, pivot)
 // and never traps.
@@ -68,7 +70,7 @@ __device__ int cholinv_smem(SmallSmem& sm, int n) {
   return sm.fail_pivot;
 }
 
-__global__ void __launch_bounds__(BT) k_cqr2_small_batched(const BatchProblem* __restrict__ probs, int count,
+__global__ void __launch_bounds__(BT, 1) k_cqr2_small_batched(const BatchProblem* __restrict__ probs, int count,
                                                            int* __restrict__ next, BatchStatus* __restrict__ status) {
   extern __shared__ double smem_raw[];
   SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
@@ -157,6 +159,11 @@ __global__ void __launch_bounds__(BT) k_cqr2_small_batched(const BatchProblem* _
       double gacc[BS];
 #pragma unroll
       for (int s = 0; s < BS; ++s) gacc[s] = 0.0;
+      // pass 2 of a least-squares problem: c = Q^T b, lane = row, per column j
+      const bool with_c = pass == 2 && pb.b != nullptr;
+      double cacc[BNMAX / 8];
+#pragma unroll
+      for (int q = 0; q < BNMAX / 8; ++q) cacc[q] = 0.0;
       for (int64_t r0 = 0; r0 < m; r0 += BPANEL) {
         for (int e = t; e < BPANEL * n; e += BT) {
           const int r = e % BPANEL, c = e / BPANEL;
@@ -175,12 +182,14 @@ __global__ void __launch_bounds__(BT) k_cqr2_small_batched(const BatchProblem* _
           qv[q] = a;
         }
         __syncthreads();  // everyone has read the panel
+        const double bv = (with_c && r0 + lane < m) ? pb.b[r0 + lane] : 0.0;
 #pragma unroll
         for (int q = 0; q < BNMAX / 8; ++q) {
           const int j = warp + 8 * q;
           if (j < n) {
             sm.P[lane * BLD + j] = qv[q];
             if (r0 + lane < m) pb.Q[r0 + lane + (int64_t)j * pb.ldq] = qv[q];
+            if (with_c) cacc[q] = fma(qv[q], bv, cacc[q]);
           }
         }
         __syncthreads();
@@ -195,6 +204,18 @@ __global__ void __launch_bounds__(BT) k_cqr2_small_batched(const BatchProblem* _
         }
         __syncthreads();
       }
+      if (with_c) {
+        // c_j = sum over lanes (fixed xor tree), kept in sm.P[j]
+#pragma unroll
+        for (int q = 0; q < BNMAX / 8; ++q) {
+          double v = cacc[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const int j = warp + 8 * q;
+          if (lane == 0 && j < n) sm.P[j] = v;
+        }
+        __syncthreads();
+      }
       if (pass == 1) {
         // W2 into S for the next CholInv (lower triangle)
 #pragma unroll
@@ -203,13 +224,34 @@ __global__ void __launch_bounds__(BT) k_cqr2_small_batched(const BatchProblem* _
         __syncthreads();
       }
     }
-    // R = R2 R1 with R2 = L2^T: R(i, j) = sum_{i<=k<=j} L2(k, i) R1(k, j)
+    // R = R2 R1 with R2 = L2^T: R(i, j) = sum_{i<=k<=j} L2(k, i) R1(k, j),
+    // also kept in T (Y2 is no longer needed) for the solve
     for (int e = t; e < n * n; e += BT) {
       const int i = e % n, j = e / n;
       double v = 0.0;
       if (i <= j)
         for (int k = i; k <= j; ++k) v = fma(sm.S[i * BLD + k], sm.R1[j * BLD + k], v);
       pb.R[i + (int64_t)j * pb.ldr] = v;
+      sm.T[j * BLD + i] = v;
+    }
+    if (pb.b != nullptr) {
+      __syncthreads();
+      if (warp == 0) {
+        // back substitution R x = c; lane l holds rows l and l + 32
+        double c0 = lane < n ? sm.P[lane] : 0.0, c1 = lane + 32 < n ? sm.P[lane + 32] : 0.0;
+        for (int j = n - 1; j >= 0; --j) {
+          const double cj = __shfl_sync(0xffffffffu, j < 32 ? c0 : c1, j & 31);
+          const double xj = cj / sm.T[j * BLD + j];
+          if (lane == (j & 31)) {
+            if (j < 32) c0 = xj;
+            else c1 = xj;
+          }
+          if (lane < j) c0 = fma(-sm.T[j * BLD + lane], xj, c0);
+          if (lane + 32 < j) c1 = fma(-sm.T[j * BLD + lane + 32], xj, c1);
+        }
+        if (lane < n) pb.x[lane] = c0;
+        if (lane + 32 < n) pb.x[lane + 32] = c1;
+      }
     }
     if (t == 0) {
       status[job].failed_pass = fail_pass;

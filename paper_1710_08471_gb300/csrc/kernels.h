@@ -155,6 +155,8 @@ struct BatchProblem {
   int64_t ldq;
   double* R;
   int64_t ldr;
+  const double* b;  // optional right-hand side (m), with x (n): least squares
+  double* x;
 };
 struct BatchStatus {
   int failed_pass;   // 0 = ok

@@ -10,11 +10,18 @@ arrive over time. The server:
 * enqueues the request's copy-in and cqr2_lstsq_rows on the slot's stream, so
   requests that arrive while others run overlap on the device, and keeps A,
   Q and R on the device until the request completes;
+* batches small requests: when the head of the queue is small (n <= 64 and
+  m n^2 <= group_work_limit), the slot takes it together with the other
+  small requests waiting in the queue (up to group_max, within the budget)
+  and runs them as one launch of the persistent grouped kernel, least-squares
+  tail included (cqr2_batch_factor with right-hand sides);
 * polls completion events, frees the memory, and admits more work.
 
 Plans are created per (slot, n) for the largest m the server accepts and are
 reused for every request of that n (cqr2_lstsq_rows takes the request's m).
-Every computation runs in libcqr2's kernels; this module only schedules.
+Whether a request runs grouped depends on its shape alone, so its result is
+the same bit for bit whatever else is in flight. Every computation runs in
+libcqr2's kernels; this module only schedules.
 """
 from __future__ import annotations
 
@@ -49,23 +56,40 @@ class Request:
         return 8 * (2 * self.m * self.n + self.n * self.n + self.m + self.n)
 
 
+GROUP_MAX_N = 64  # the grouped kernel's largest n
+
+
 class CudaExecutor:
     """Runs requests on CUDA stream slots through cqr2_lstsq_rows, one plan
-    per (slot, n) sized for the largest m."""
+    per (slot, n) sized for the largest m, and groups of small requests
+    through one grouped launch per slot (a cqr2 batch on the slot's stream).
+    group_max = 1 turns grouping off."""
 
-    def __init__(self, slots: int, precision: int, m_max: int, n_values, keep_outputs: bool = False):
+    def __init__(self, slots: int, precision: int, m_max: int, n_values, keep_outputs: bool = False,
+                 group_max: int = 64, group_work_limit: int = 1 << 24):
         import torch
 
         self.torch = torch
         self.precision = precision
         self.m_max = int(m_max)
         self.keep = keep_outputs
+        self.group_max = int(group_max)
+        self.group_work_limit = int(group_work_limit)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.plans = [dict() for _ in range(slots)]
+        self.batches = []
         self.workspace_bytes = 0
         for s in range(slots):
             for n in n_values:
-                self._plan(s, n)
+                if not self.groupable(self.m_max, n):
+                    self._plan(s, n)
+        if self.group_max > 1:
+            # the batch routes by the same rule (n <= 64, m n^2 <= the limit)
+            self.batches = [cq.Batch(self.group_max, small_work_limit=self.group_work_limit, streams=1,
+                                     stream=self.streams[s]) for s in range(slots)]
+
+    def groupable(self, m: int, n: int) -> bool:
+        return self.group_max > 1 and n <= GROUP_MAX_N and m * n * n <= self.group_work_limit
 
     @property
     def slots(self) -> int:
@@ -101,6 +125,27 @@ class CudaExecutor:
             ev.record(s)
         return (ev, (A, b, Q, R, x), plan)
 
+    def submit_group(self, reqs: list, slot: int):
+        """Enqueue the copy-in of every request of the group and one grouped
+        launch (factorization and least-squares tail) on the slot's stream."""
+        torch = self.torch
+        s = self.streams[slot]
+        bufs = []
+        with torch.cuda.stream(s):
+            for r in reqs:
+                A = cq.empty_colmajor(r.m, r.n, device="cuda")
+                A.copy_(r.A_src)
+                b = r.b_src.clone()
+                Q = cq.empty_colmajor(r.m, r.n, device="cuda")
+                R = cq.empty_colmajor(r.n, r.n, device="cuda")
+                x = torch.empty(r.n, dtype=torch.float64, device="cuda")
+                bufs.append((A, Q, R, b, x))
+            batch = self.batches[slot]
+            batch.factor(bufs, sync=False)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return (ev, bufs, batch)
+
     def poll(self, handle) -> bool:
         return handle[0].query()
 
@@ -114,11 +159,23 @@ class CudaExecutor:
         if self.keep:
             r.Q, r.R = Q, R
 
+    def finish_group(self, reqs: list, handle) -> None:
+        ev, bufs, batch = handle
+        infos = batch.info()  # the slot's stream has finished: no wait
+        for r, (A, Q, R, b, x), inf in zip(reqs, bufs, infos):
+            r.status = inf.status
+            r.x = x
+            if self.keep:
+                r.Q, r.R = Q, R
+
     def close(self) -> None:
         for d in self.plans:
             for p in d.values():
                 p.close()
         self.plans = []
+        for b in self.batches:
+            b.close()
+        self.batches = []
 
 
 class Server:
@@ -129,36 +186,77 @@ class Server:
 
     def __init__(self, budget_bytes: float, slots: int = 8, precision: int = cq.CQR2_FP64, m_max: int = 262144,
                  n_values=(16, 32, 64, 128, 256), keep_outputs: bool = False, executor=None, clock=None,
-                 sleep=None):
+                 sleep=None, group_max: int = 64, group_work_limit: int = 1 << 24):
         self.exec = executor if executor is not None else CudaExecutor(slots, precision, m_max, n_values,
-                                                                       keep_outputs)
+                                                                       keep_outputs, group_max, group_work_limit)
         self.clock = clock or time.perf_counter
         self.sleep = sleep or time.sleep
         self.budget = float(budget_bytes)
-        self.busy = [None] * self.exec.slots  # (request, handle)
+        self.busy = [None] * self.exec.slots  # (requests, handle, grouped)
         self.inflight_bytes = 0
         self.peak_inflight_bytes = 0
         self.admitted: list[int] = []
+        self.group_launches = 0
+        self.grouped_requests = 0
 
     @property
     def workspace_bytes(self) -> int:
         return self.exec.workspace_bytes
 
-    def _submit(self, r: Request, slot: int, t0: float):
-        handle = self.exec.submit(r, slot)
-        r.t_admit = self.clock() - t0
-        r.slot = slot
-        self.busy[slot] = (r, handle)
-        self.inflight_bytes += r.bytes
+    def _groupable(self, r: Request) -> bool:
+        g = getattr(self.exec, "groupable", None)
+        return g is not None and g(r.m, r.n)
+
+    def _submit(self, reqs: list, slot: int, t0: float):
+        grouped = self._groupable(reqs[0])
+        handle = self.exec.submit_group(reqs, slot) if grouped else self.exec.submit(reqs[0], slot)
+        t = self.clock() - t0
+        for r in reqs:
+            r.t_admit = t
+            r.slot = slot
+            self.inflight_bytes += r.bytes
+            self.admitted.append(r.id)
+        self.busy[slot] = (reqs, handle, grouped)
         self.peak_inflight_bytes = max(self.peak_inflight_bytes, self.inflight_bytes)
-        self.admitted.append(r.id)
+        if grouped:
+            self.group_launches += 1
+            self.grouped_requests += len(reqs)
 
     def _retire(self, slot: int, t0: float):
-        r, handle = self.busy[slot]
-        r.t_done = self.clock() - t0
-        self.exec.finish(r, handle)
+        reqs, handle, grouped = self.busy[slot]
+        t = self.clock() - t0
+        for r in reqs:
+            r.t_done = t
+        if grouped:
+            self.exec.finish_group(reqs, handle)
+        else:
+            self.exec.finish(reqs[0], handle)
         self.busy[slot] = None
-        self.inflight_bytes -= r.bytes
+        for r in reqs:
+            self.inflight_bytes -= r.bytes
+
+    def _take(self, queue, limit: float):
+        """The head of the queue and, if it is small, the other small requests
+        waiting behind it (in queue order, up to the group size, within the
+        budget)."""
+        head = queue.popleft()
+        reqs = [head]
+        if not self._groupable(head):
+            return reqs
+        room = limit - self.inflight_bytes - head.bytes
+        gmax = self.exec.group_max
+        keep = collections.deque()
+        while queue and len(reqs) < gmax:
+            r = queue.popleft()
+            if self._groupable(r) and r.bytes <= room:
+                reqs.append(r)
+                room -= r.bytes
+            else:
+                keep.append(r)
+        keep.extend(queue)
+        queue.clear()
+        queue.extend(keep)
+        return reqs
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         """Serve `requests`. With realtime, a request is not admitted before
@@ -176,7 +274,7 @@ class Server:
                 queue.append(pending.popleft())
             for s in range(slots):
                 if self.busy[s] is not None and self.exec.poll(self.busy[s][1]):
-                    done.append(self.busy[s][0])
+                    done.extend(self.busy[s][0])
                     self._retire(s, t0)
             while queue and queue[0].bytes > limit:
                 # larger than the whole budget: it can never be admitted
@@ -188,7 +286,7 @@ class Server:
                 if not queue:
                     break
                 if self.busy[s] is None and self.inflight_bytes + queue[0].bytes <= limit:
-                    self._submit(queue.popleft(), s, t0)
+                    self._submit(self._take(queue, limit), s, t0)
             if not queue and pending and realtime:
                 # idle until the next arrival
                 wait = pending[0].t_arrival - (self.clock() - t0)
@@ -206,6 +304,8 @@ class Server:
             "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
             "workspace_bytes": self.workspace_bytes,
             "peak_inflight_gb": self.peak_inflight_bytes / 1e9,
+            "group_launches": self.group_launches,
+            "grouped_requests": self.grouped_requests,
         }
 
     def close(self):
@@ -223,7 +323,8 @@ def percentile(sorted_vals, q: float) -> float:
 
 def run_workload(count: int, rate: float, seed: int = 100, precision: int = cq.CQR2_FP64, slots: int = 8,
                  budget: float = 64e9, m_max: int = 262144, n_values=(16, 32, 64, 128, 256),
-                 realtime: bool = True, pool: "InputPool | None" = None) -> dict:
+                 realtime: bool = True, pool: "InputPool | None" = None, group_max: int = 64,
+                 group_work_limit: int = 1 << 24) -> dict:
     """Serve a seeded least-squares request stream (synth.request_stream:
     Poisson arrivals at `rate`, m uniform in [1024, m_max], n uniform over
     n_values, kappa log-uniform in [1, 1e5]) and return latency/throughput."""
@@ -232,7 +333,8 @@ def run_workload(count: int, rate: float, seed: int = 100, precision: int = cq.C
     stream = synth.request_stream(count, seed=seed, rate=rate, m_lo=1024, m_hi=m_max, n_choices=tuple(n_values))
     pool = pool or InputPool(m_max, n_values, seed=seed)
     reqs = [pool.request(r["id"], r["t"], r["m"], r["n"], r["kappa"]) for r in stream]
-    srv = Server(budget, slots=slots, precision=precision, m_max=m_max, n_values=n_values)
+    srv = Server(budget, slots=slots, precision=precision, m_max=m_max, n_values=n_values, group_max=group_max,
+                 group_work_limit=group_work_limit)
     try:
         stats = srv.run(reqs, realtime=realtime)
     finally:
@@ -241,7 +343,8 @@ def run_workload(count: int, rate: float, seed: int = 100, precision: int = cq.C
     flops = sum(4.0 * r.m * r.n * r.n + 5.0 * r.n ** 3 / 3.0 + 2.0 * r.m * r.n for r in done)
     stats["tflops"] = flops / stats["seconds"] / 1e12 if stats["seconds"] > 0 else float("nan")
     stats.update({"requests": count, "rate_per_s": rate, "slots": slots, "precision": precision,
-                  "budget_gb": budget / 1e9, "m_max": m_max, "n_values": list(n_values)})
+                  "budget_gb": budget / 1e9, "m_max": m_max, "n_values": list(n_values), "group_max": group_max,
+                  "group_work_limit": group_work_limit})
     return stats
 
 
@@ -256,12 +359,15 @@ def main(argv=None) -> None:
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--precision", type=int, default=cq.CQR2_OZAKI_BF16)
     ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--group-max", type=int, default=64, help="small requests per grouped launch (1 = no grouping)")
+    ap.add_argument("--group-work-limit", type=int, default=1 << 24, help="grouped when n <= 64 and m n^2 <= this")
     args = ap.parse_args(argv)
     pool = InputPool(262144, (16, 32, 64, 128, 256), seed=args.seed)
     out = {"continuous": run_workload(args.requests, args.rate, args.seed, args.precision, args.slots,
-                                      args.budget_gb * 1e9, pool=pool),
+                                      args.budget_gb * 1e9, pool=pool, group_max=args.group_max,
+                                      group_work_limit=args.group_work_limit),
            "one_at_a_time": run_workload(args.requests, args.rate, args.seed, args.precision, 1,
-                                         args.budget_gb * 1e9, pool=pool)}
+                                         args.budget_gb * 1e9, pool=pool, group_max=1)}
     print(json.dumps(out))
 
 

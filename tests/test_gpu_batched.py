@@ -159,6 +159,95 @@ def test_batch_result_same_alone_and_in_mix(cq):
             assert np.array_equal(Q, mixed[i][0]) and np.array_equal(R, mixed[i][1]), i
 
 
+def _lstsq_problems(cq, shapes, seed0=0):
+    import torch
+
+    mats, rhs, probs = [], [], []
+    for i, (m, n, kappa) in enumerate(shapes):
+        A = synth.make_matrix(m, n, kappa, seed=seed0 + i)
+        b = synth.make_rhs(m, seed=seed0 + 1000 + i)
+        mats.append(A)
+        rhs.append(b)
+        probs.append((to_dev(A), cq.empty_colmajor(m, n, device="cuda"), cq.empty_colmajor(n, n, device="cuda"),
+                      to_dev(b), torch.empty(n, dtype=torch.float64, device="cuda")))
+    return mats, rhs, probs
+
+
+def check_x(A, b, x, kappa):
+    xo = oracle.lstsq(A, b)
+    k = kappa or 2.0
+    assert np.linalg.norm(x - xo) <= 1e-12 * k * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("limit", [1 << 40, None])
+def test_batch_lstsq(cq, limit):
+    """Least squares through the batch: the grouped kernel's tail (c = Q^T b
+    while the final Q is formed, back substitution in one warp) and, with the
+    default routing, the planned problems' cqr2_lstsq_rows."""
+    shapes = MIXED if limit is None else SMALL * 2
+    mats, rhs, probs = _lstsq_problems(cq, shapes, seed0=400)
+    kw = {} if limit is None else {"small_work_limit": limit}
+    with cq.Batch(len(probs), **kw) as b:
+        infos = b.factor(probs)
+    for A, bv, pr, inf, (m, n, kappa) in zip(mats, rhs, probs, infos, shapes):
+        assert inf.status == 0
+        check(A, to_host(pr[1]), to_host(pr[2]), kappa)
+        check_x(A, bv, to_host(pr[4]), kappa)
+
+
+def test_batch_lstsq_ragged_and_extremes(cq):
+    # n = 1, n = 64 with m = n, row counts off the 32-row panel, and a
+    # right-hand side in the range of A (zero residual): x = the generating
+    # coefficients
+    shapes = [(1, 1, None), (64, 64, 10.0), (65, 63, 1e2), (33, 32, None), (4097, 64, 1e3), (31, 31, 1e1)]
+    mats, rhs, probs = _lstsq_problems(cq, shapes, seed0=500)
+    xs = []
+    for i, (A, (m, n, _)) in enumerate(zip(mats, shapes)):
+        xt = np.random.default_rng(i).standard_normal(n)
+        rhs[i] = A @ xt
+        xs.append(xt)
+        probs[i][3].copy_(to_dev(rhs[i]))
+    with cq.Batch(len(probs), small_work_limit=1 << 40) as b:
+        infos = b.factor(probs)
+    for A, bv, pr, inf, xt, (m, n, kappa) in zip(mats, rhs, probs, infos, xs, shapes):
+        assert inf.status == 0
+        x = to_host(pr[4])
+        check_x(A, bv, x, kappa)
+        assert np.linalg.norm(x - xt) <= 1e-12 * (kappa or 2.0) * np.linalg.norm(xt)
+
+
+def test_batch_async_info_and_reuse(cq):
+    """factor(sync=False) then info(): the same outcomes as the synchronous
+    form; a second call on the batch waits for the first."""
+    shapes = [(500, 16, None), (600, 16, None), (3000, 128, 1e3), (800, 64, 1e2)]
+    mats, rhs, probs = _lstsq_problems(cq, shapes, seed0=600)
+    mats[1][:, 3] = 0.0
+    probs[1][0].copy_(to_dev(mats[1]))
+    with cq.Batch(len(probs)) as b:
+        assert b.factor(probs, sync=False) is None
+        infos = b.info()
+        assert [i.status for i in infos] == [0, cq.CQR2_ERR_NOT_SPD, 0, 0]
+        assert infos[1].failed_pass == 1 and infos[1].failed_pivot == 3
+        x0 = [to_host(p[4]) for p in probs]
+        b.factor(probs[:3], sync=False)
+        b.factor(probs[:3], sync=False)  # reuses the descriptors after the first finished
+        infos = b.info()
+        assert len(infos) == 3 and infos[1].status == cq.CQR2_ERR_NOT_SPD
+    for i in (0, 2):
+        assert np.array_equal(to_host(probs[i][4]), x0[i])
+        check_x(mats[i], rhs[i], x0[i], shapes[i][2])
+
+
+def test_batch_lstsq_same_alone_and_in_mix(cq):
+    mats, rhs, probs = _lstsq_problems(cq, MIXED, seed0=700)
+    with cq.Batch(len(probs)) as b:
+        b.factor(probs)
+        mixed = [to_host(p[4]) for p in probs]
+        for i, pr in enumerate(probs):
+            b.factor([pr])
+            assert np.array_equal(to_host(pr[4]), mixed[i]), i
+
+
 def test_autotune_records_table(cq):
     res = cq.cqr2_autotune(50000, 128)
     assert res["candidates"] >= 4 and res["gram_ctas"] in (1, 2, 4, 8) and res["ms"] > 0

@@ -28,10 +28,11 @@ def env():
     return cq, serving, pool, stream, m_max
 
 
-def _serve(env, slots, precision=0, budget=8e9, realtime=False):
+def _serve(env, slots, precision=0, budget=8e9, realtime=False, group_max=64):
     cq, serving, pool, stream, m_max = env
     reqs = [pool.request(r["id"], r["t"], r["m"], r["n"], r["kappa"]) for r in stream]
-    srv = serving.Server(budget, slots=slots, precision=precision, m_max=m_max, n_values=(16, 32, 64, 128))
+    srv = serving.Server(budget, slots=slots, precision=precision, m_max=m_max, n_values=(16, 32, 64, 128),
+                         group_max=group_max)
     try:
         stats = srv.run(reqs, realtime=realtime)
     finally:
@@ -39,11 +40,14 @@ def _serve(env, slots, precision=0, budget=8e9, realtime=False):
     return reqs, stats
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-11)])
-def test_serving_matches_oracle(env, precision, tol):
+@pytest.mark.parametrize("precision,tol,group_max", [(0, 1e-12, 64), (1, 1e-11, 64), (0, 1e-12, 1)])
+def test_serving_matches_oracle(env, precision, tol, group_max):
     cq, serving, pool, stream, m_max = env
-    reqs, stats = _serve(env, slots=6, precision=precision)
+    reqs, stats = _serve(env, slots=6, precision=precision, group_max=group_max)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    # small requests (n <= 64, m n^2 <= 2^24) ran in grouped launches
+    small = sum(1 for r in reqs if r.n <= 64 and r.m * r.n * r.n <= 1 << 24)
+    assert small > 0 and stats["grouped_requests"] == (small if group_max > 1 else 0)
     for r in reqs[:12]:
         A = to_host(r.A_src)
         b = to_host(r.b_src)
