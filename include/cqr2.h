@@ -78,6 +78,14 @@ typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2
                              (Section V): accurate to kappa(A) near 1e12, where
                              plain CholeskyQR2 breaks down. Breakdown passes
                              are reported as 1 (shifted), 2 and 3. */
+#define CQR2_INPLACE 0x8u /* allow dQ == dA (with ldq == lda): Q overwrites A.
+                             Every path reads each part of A before Q lands on
+                             it: FP64 n <= 256 stages each row panel on chip
+                             before writing it, wider FP64 forms Q1 in the
+                             plan's workspace, and the split-precision Q-form
+                             reads only A's slices. Without this flag dQ == dA
+                             is CQR2_ERR_INVALID_ARG. Q and A must never
+                             overlap partially. */
 #define CQR2_GRAPH 0x2u /* capture the launch sequence of a factorization in
                            a CUDA graph and replay it while the call's
                            pointers, leading dimensions and m repeat; needs a
@@ -123,9 +131,10 @@ cqr2_status_t cqr2_factor(cqr2_plan_t plan, const double* dA, int64_t lda, doubl
 /* Least squares min_x ||A x - b||_2 through CholeskyQR2 (the paper names
  * least squares as the use, Section I; the solve itself is this library's
  * reading): factor A = QR, c = Q^T b, then x solves R x = c by back
- * substitution. db: m-vector, dx: n-vector (device). dQ (m x n, ldq) is
- * required (Q is staged there); dR may be NULL, else receives R. info as in
- * cqr2_factor. */
+ * substitution. db: m-vector, dx: n-vector (device). dQ (m x n, ldq)
+ * receives Q; it may be NULL, and then Q goes to an m x n buffer the plan
+ * allocates on the first such call and keeps (CQR2_ERR_OOM if that fails).
+ * dR may be NULL, else receives R. info as in cqr2_factor. */
 cqr2_status_t cqr2_lstsq(cqr2_plan_t plan, const double* dA, int64_t lda, const double* db, double* dx,
                          double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info);
 

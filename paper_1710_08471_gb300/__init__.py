@@ -150,7 +150,10 @@ def cqr2_factor_rows(plan, m, n, A, Q, R, sync: bool = True) -> Info | None:
 def cqr2_lstsq_rows(plan, m, n, A, b, x, Q, R=None, sync: bool = True) -> Info | None:
     """cqr2_lstsq for an m-row matrix on a plan created for at least m rows."""
     a, lda = _mat(A, m, n, "A")
-    q, ldq = _mat(Q, m, n, "Q")
+    if Q is not None:
+        q, ldq = _mat(Q, m, n, "Q")
+    else:
+        q, ldq = None, m  # Q into the plan's own buffer
     if R is not None:
         r, ldr = _mat(R, n, n, "R")
     else:
@@ -340,9 +343,10 @@ class Plan:
     """Owns a cqr2 plan for m x n factorizations on the current device."""
 
     def __init__(self, m: int, n: int, precision: int = CQR2_FP64, fused: bool = False, stream=None,
-                 graph: bool = False):
+                 graph: bool = False, shifted: bool = False, inplace: bool = False):
         self.m, self.n = int(m), int(n)
-        flags = (CQR2_FUSED if fused else 0) | (N.CQR2_GRAPH if graph else 0)
+        flags = ((CQR2_FUSED if fused else 0) | (N.CQR2_GRAPH if graph else 0) | (N.CQR2_SHIFTED if shifted else 0)
+                 | (N.CQR2_INPLACE if inplace else 0))
         self.handle = cqr2_plan_create(self.m, self.n, precision, flags, stream)
 
     def factor_rows(self, A, Q=None, R=None, sync: bool = True):
@@ -355,10 +359,12 @@ class Plan:
         info = cqr2_factor_rows(self.handle, m, self.n, A, Q, R, sync)
         return Q, R, info
 
-    def lstsq_rows(self, A, b, Q=None, R=None, x=None, sync: bool = True):
+    def lstsq_rows(self, A, b, Q=None, R=None, x=None, sync: bool = True, keep_q: bool = True):
+        """Least squares for an m-row matrix. With keep_q=False and no Q, Q
+        goes to the plan's own buffer instead of a new tensor."""
         torch = _torch()
         m = A.shape[0]
-        if Q is None:
+        if Q is None and keep_q:
             Q = empty_colmajor(m, self.n, device=A.device)
         if x is None:
             x = torch.empty(self.n, dtype=torch.float64, device=A.device)

@@ -24,6 +24,8 @@ CQR2_OZAKI_BF16 = 1
 CQR2_OZAKI_BF16_S6 = 2
 CQR2_FUSED = 0x1
 CQR2_GRAPH = 0x2
+CQR2_SHIFTED = 0x4
+CQR2_INPLACE = 0x8
 CQR2_NUM_STAGES = 11
 
 

@@ -55,6 +55,7 @@ struct cqr2_plan_st {
   DevStatus* h_st = nullptr;  // pinned host copy
   // device staging for cqr2_factor_host (allocated on its first call)
   double* hA_dev = nullptr;
+  double* lsQ = nullptr;  // Q of least-squares calls given no dQ (m x n, on demand)
   double* hQ_dev = nullptr;
   double* hR_dev = nullptr;
   // cqr2_factor_host overlaps its copies with the factorization: A arrives
@@ -400,6 +401,12 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
     } else if (p->small) {
       TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
       TRY(qform_small(dA, lda, m, n, p->Rp, dQ, ldq, s));
+    } else if ((const void*)dA == (const void*)dQ) {
+      // in place: the tiled multiply may not write over its input, so Q0 is
+      // formed in the workspace and copied over A
+      TRY(plan_apply_rinv(p, m, dA, lda, p->Q1, p->m, s));
+      TRY(cudaMemcpy2DAsync(dQ, (size_t)ldq * sizeof(double), p->Q1, (size_t)p->m * sizeof(double),
+                            (size_t)m * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, s));
     } else {
       TRY(plan_apply_rinv(p, m, dA, lda, dQ, ldq, s));
     }
@@ -413,6 +420,12 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
 }
 
 bool bad_ld(int64_t ld, int64_t rows) { return ld < std::max<int64_t>(1, rows); }
+
+// Q may be A itself only on a CQR2_INPLACE plan, with the same leading dimension.
+bool bad_alias(const cqr2_plan_st* p, const double* dA, int64_t lda, const double* dQ, int64_t ldq) {
+  if ((const void*)dA != (const void*)dQ) return false;
+  return !(p->flags & CQR2_INPLACE) || lda != ldq;
+}
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -442,7 +455,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (n < 1 || m < n || n > 65535) return CQR2_ERR_INVALID_ARG;
   if (precision != CQR2_FP64 && precision != CQR2_OZAKI_BF16 && precision != CQR2_OZAKI_BF16_S6)
     return CQR2_ERR_INVALID_ARG;
-  if (flags & ~(CQR2_FUSED | CQR2_GRAPH | CQR2_SHIFTED)) return CQR2_ERR_INVALID_ARG;
+  if (flags & ~(CQR2_FUSED | CQR2_GRAPH | CQR2_SHIFTED | CQR2_INPLACE)) return CQR2_ERR_INVALID_ARG;
   const int oz_S = precision == CQR2_OZAKI_BF16 ? 7 : (precision == CQR2_OZAKI_BF16_S6 ? 6 : 0);
   if (oz_S && !ozaki_supported((int)n, oz_S)) return CQR2_ERR_UNSUPPORTED;
   int dev = 0;
@@ -589,6 +602,7 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
   cudaFree(plan->hx_partial);
   cudaFree(plan->Tsolve);
   cudaFree(plan->hA_dev);
+  cudaFree(plan->lsQ);
   cudaFree(plan->hQ_dev);
   cudaFree(plan->hR_dev);
   cudaFree(plan->ws);
@@ -606,7 +620,7 @@ cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64
   if (!p || !dA || !dQ || !dR) return CQR2_ERR_INVALID_ARG;
   if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
   if (bad_ld(lda, m) || bad_ld(ldq, m) || bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
-  if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
+  if (bad_alias(p, dA, lda, dQ, ldq)) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
   if ((r = set_rows(p, m)) != CQR2_OK) return r;
@@ -725,13 +739,23 @@ cqr2_status_t cqr2_lstsq(cqr2_plan_t p, const double* dA, int64_t lda, const dou
 
 cqr2_status_t cqr2_lstsq_rows(cqr2_plan_t p, int64_t m, const double* dA, int64_t lda, const double* db, double* dx,
                               double* dQ, int64_t ldq, double* dR, int64_t ldr, cqr2_info_t* info) {
-  if (!p || !dA || !db || !dx || !dQ) return CQR2_ERR_INVALID_ARG;
+  if (!p || !dA || !db || !dx) return CQR2_ERR_INVALID_ARG;
   if (m < p->n || m > p->m) return CQR2_ERR_INVALID_ARG;
-  if (bad_ld(lda, m) || bad_ld(ldq, m)) return CQR2_ERR_INVALID_ARG;
+  if (bad_ld(lda, m) || (dQ && bad_ld(ldq, m))) return CQR2_ERR_INVALID_ARG;
   if (dR && bad_ld(ldr, p->n)) return CQR2_ERR_INVALID_ARG;
-  if ((const void*)dA == (const void*)dQ) return CQR2_ERR_INVALID_ARG;
+  if (dQ && bad_alias(p, dA, lda, dQ, ldq)) return CQR2_ERR_INVALID_ARG;
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
+  if (!dQ) {
+    // Q into the plan's own m x n buffer, allocated once
+    if (!p->lsQ && cudaMalloc(&p->lsQ, (size_t)p->m * p->n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      p->lsQ = nullptr;
+      return CQR2_ERR_OOM;
+    }
+    dQ = p->lsQ;
+    ldq = p->m;
+  }
   if ((r = set_rows(p, m)) != CQR2_OK) return r;
   double* R = dR ? dR : p->Rf;
   const int64_t ldR = dR ? ldr : p->n;

@@ -80,3 +80,17 @@ def test_product_package_does_not_import_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
                 assert "oracle/" not in src, f
+
+
+def test_header_constants_match_binding():
+    """The Python binding's flag, precision and status values are the ones
+    the C header defines."""
+    from paper_1710_08471_gb300 import _native
+
+    hdr = open(os.path.join(ROOT, "include", "cqr2.h")).read()
+    vals = {k: int(v, 0) for k, v in re.findall(r"#define\s+(CQR2_[A-Z_]+)\s+(0x[0-9a-fA-F]+)u", hdr)}
+    vals.update({k: int(v) for k, v in re.findall(r"\b(CQR2_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)})
+    for name in ("CQR2_FUSED", "CQR2_GRAPH", "CQR2_SHIFTED", "CQR2_INPLACE", "CQR2_FP64", "CQR2_OZAKI_BF16",
+                 "CQR2_OZAKI_BF16_S6", "CQR2_OK", "CQR2_ERR_INVALID_ARG", "CQR2_ERR_NOT_SPD", "CQR2_ERR_OOM",
+                 "CQR2_ERR_TIMEOUT", "CQR2_ERR_UNSUPPORTED"):
+        assert getattr(_native, name) == vals[name], name
