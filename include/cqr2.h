@@ -236,16 +236,23 @@ typedef struct cqr2_batch_st* cqr2_batch_t;
  *   problem at a time, FP64 whatever the batch precision).
  * streams: the other problems run on per-(n, stream) plans spread over this
  *   many streams (1..16) forked from and joined to the batch stream.
- * fused: use CQR2_FUSED for those plans. */
+ * fused: use CQR2_FUSED for those plans.
+ * graph: when a call repeats the previous call's problem list exactly (same
+ *   descriptors, same order), capture its whole launch sequence -- the
+ *   grouped launch and every planned problem's kernels on the forked
+ *   streams -- into a CUDA graph, and replay that graph while the list keeps
+ *   repeating. Needs a non-NULL batch stream; 0 = off. */
 typedef struct {
   int64_t small_work_limit;
   int32_t streams;
   int32_t fused;
+  int32_t graph;
 } cqr2_batch_config_t;
 
 /* Create a batch context for up to max_count problems per call, with the
  * precision used by the planned problems (cqr2_precision_t). cfg may be NULL
- * for the defaults (the tuned small-problem limit, 4 streams, fused). Plans
+ * for the defaults (the tuned small-problem limit, 4 streams, fused, no
+ * graph). Plans
  * are created lazily per (n, stream) and grow to the largest m seen. */
 cqr2_status_t cqr2_batch_create(cqr2_batch_t* batch, int32_t max_count, int32_t precision,
                                 const cqr2_batch_config_t* cfg, void* stream);

@@ -274,11 +274,11 @@ class Batch:
     """Many independent CholeskyQR2 factorizations per call (cqr2_batch_*)."""
 
     def __init__(self, max_count: int, precision: int = CQR2_FP64, small_work_limit: int | None = None,
-                 streams: int | None = None, fused: bool = True, stream=None):
+                 streams: int | None = None, fused: bool = True, stream=None, graph: bool = False):
         cfg = None
-        if small_work_limit is not None or streams is not None:
+        if small_work_limit is not None or streams is not None or graph:
             cfg = N.BatchConfig(int(small_work_limit if small_work_limit is not None else 32768 * 64 * 64),
-                                int(streams or 4), 1 if fused else 0)
+                                int(streams or 4), 1 if fused else 0, 1 if graph else 0)
         h = C.c_void_p()
         N.check(N.load().cqr2_batch_create(C.byref(h), int(max_count), precision,
                                            C.byref(cfg) if cfg is not None else None, _stream_handle(stream)),

@@ -43,7 +43,7 @@ class Problem(C.Structure):
 
 class BatchConfig(C.Structure):
     """cqr2_batch_config_t"""
-    _fields_ = [("small_work_limit", C.c_int64), ("streams", C.c_int32), ("fused", C.c_int32)]
+    _fields_ = [("small_work_limit", C.c_int64), ("streams", C.c_int32), ("fused", C.c_int32), ("graph", C.c_int32)]
 
 
 class TuneResult(C.Structure):

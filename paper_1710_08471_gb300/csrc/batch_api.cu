@@ -51,6 +51,13 @@ struct cqr2_batch_st {
   int32_t last_count = 0;
   std::vector<int> last_small;                 // problem index per grouped job
   std::vector<int> last_used;                  // problem index per planned status word
+  // graph replay of a repeating problem list (cfg.graph)
+  std::vector<cqr2_problem_t> gkey;            // the previous call's list
+  bool gkey_valid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;             // captured for gkey, if any
+  std::vector<int> g_small, g_used;            // its outcome locations
+  int64_t replays = 0;
 };
 
 namespace {
@@ -158,6 +165,55 @@ cqr2_status_t batch_enqueue(cqr2_batch_t b, const cqr2_problem_t* problems, int3
   return CQR2_OK;
 }
 
+bool same_problem(const cqr2_problem_t& a, const cqr2_problem_t& c) {
+  return a.m == c.m && a.n == c.n && a.A == c.A && a.lda == c.lda && a.Q == c.Q && a.ldq == c.ldq && a.R == c.R &&
+         a.ldr == c.ldr && a.b == c.b && a.x == c.x;
+}
+
+void drop_graph(cqr2_batch_t b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+// cfg.graph: the first call of a list runs eagerly (plans get created and
+// sized outside any capture); when the next call repeats it, that call's
+// sequence is captured and launched, and later repeats replay the graph.
+cqr2_status_t batch_enqueue_graph(cqr2_batch_t b, const cqr2_problem_t* problems, int32_t count) {
+  bool same = b->gkey_valid && (int32_t)b->gkey.size() == count;
+  for (int i = 0; same && i < count; ++i) same = same_problem(b->gkey[i], problems[i]);
+  if (!same) {
+    drop_graph(b);
+    b->gkey.assign(problems, problems + count);
+    b->gkey_valid = false;
+    const cqr2_status_t r = batch_enqueue(b, problems, count);
+    b->gkey_valid = r == CQR2_OK;
+    return r;
+  }
+  if (!b->gexec) {
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CQR2_ERR_CUDA;
+    const cqr2_status_t r = batch_enqueue(b, problems, count);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (r != CQR2_OK || ce != cudaSuccess || cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      b->gexec = nullptr;
+      b->gkey_valid = false;
+      cudaGetLastError();
+      return r != CQR2_OK ? r : CQR2_ERR_CUDA;
+    }
+    b->graph = g;
+    b->g_small = b->last_small;
+    b->g_used = b->last_used;
+  } else {
+    b->last_small = b->g_small;
+    b->last_used = b->g_used;
+    ++b->replays;
+  }
+  return cudaGraphLaunch(b->gexec, b->stream) == cudaSuccess ? CQR2_OK : CQR2_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -223,6 +279,8 @@ void cqr2_batch_destroy(cqr2_batch_t b) {
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
   cudaFree(b->d_probs);
   cudaFree(b->d_status);
   cudaFree(b->d_next);
@@ -251,7 +309,8 @@ cqr2_status_t cqr2_batch_factor(cqr2_batch_t b, const cqr2_problem_t* problems, 
   b->last_small.clear();
   b->last_used.clear();
   // whatever gets enqueued, the next call waits for it
-  const cqr2_status_t r = batch_enqueue(b, problems, count);
+  const cqr2_status_t r = b->cfg.graph && b->stream ? batch_enqueue_graph(b, problems, count)
+                                                    : batch_enqueue(b, problems, count);
   const bool recorded = cudaEventRecord(b->done, b->stream) == cudaSuccess;
   b->pending = recorded;
   if (r != CQR2_OK || !recorded) {

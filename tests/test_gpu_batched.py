@@ -173,10 +173,10 @@ def _lstsq_problems(cq, shapes, seed0=0):
     return mats, rhs, probs
 
 
-def check_x(A, b, x, kappa):
+def check_x(A, b, x, kappa, scale=1.0):
     xo = oracle.lstsq(A, b)
     k = kappa or 2.0
-    assert np.linalg.norm(x - xo) <= 1e-12 * k * np.linalg.norm(xo)
+    assert np.linalg.norm(x - xo) <= scale * 1e-12 * k * np.linalg.norm(xo)
 
 
 @pytest.mark.parametrize("limit", [1 << 40, None])
@@ -246,6 +246,51 @@ def test_batch_lstsq_same_alone_and_in_mix(cq):
         for i, pr in enumerate(probs):
             b.factor([pr])
             assert np.array_equal(to_host(pr[4]), mixed[i]), i
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_graph_replay(cq, prec):
+    """cfg.graph: the first call runs eagerly, the repeat is captured, later
+    repeats replay the graph. Every call gives the eager batch's results bit
+    for bit, a replay recomputes from the inputs' current contents (A scaled
+    by 2 gives the same Q and 2 R exactly), and a new list runs eagerly."""
+    import torch
+
+    shapes = MIXED[:6] + MIXED[-4:]
+    mats, rhs, probs = _lstsq_problems(cq, shapes, seed0=800)
+    with cq.Batch(len(probs), precision=prec) as b:
+        assert all(i.status == 0 for i in b.factor(probs))
+        ref = [(to_host(p[1]), to_host(p[2]), to_host(p[4])) for p in probs]
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with cq.Batch(len(probs), precision=prec, stream=s, graph=True) as b:
+        for call in range(4):
+            for p in probs:
+                p[1].zero_(), p[2].zero_(), p[4].zero_()
+            torch.cuda.synchronize()
+            infos = b.factor(probs)
+            assert all(i.status == 0 for i in infos), call
+            for i, p in enumerate(probs):
+                assert np.array_equal(to_host(p[1]), ref[i][0]), (call, i)
+                assert np.array_equal(to_host(p[2]), ref[i][1]), (call, i)
+                assert np.array_equal(to_host(p[4]), ref[i][2]), (call, i)
+        for p in probs:
+            p[0].mul_(2.0)
+        torch.cuda.synchronize()
+        b.factor(probs)  # replay on the new contents
+        for i, p in enumerate(probs):
+            assert np.array_equal(to_host(p[1]), ref[i][0]), i
+            assert np.array_equal(to_host(p[2]), 2.0 * ref[i][1]), i
+        for p in probs:
+            p[0].mul_(0.5)
+        torch.cuda.synchronize()
+        # a different list: eager again, still correct
+        sub = probs[::2]
+        infos = b.factor(sub)
+        for (A, bv, pr, (m, n, kappa)), inf in zip(list(zip(mats, rhs, probs, shapes))[::2], infos):
+            assert inf.status == 0
+            check(A, to_host(pr[1]), to_host(pr[2]), kappa, 1.0 if prec == 0 else 10.0)
+            check_x(A, bv, to_host(pr[4]), kappa, 1.0 if prec == 0 else 10.0)
 
 
 def test_autotune_records_table(cq):
