@@ -32,8 +32,64 @@ struct SmallSmem {
   double T[BNMAX * BLD];   // Y = L^-1 (lower)
   double R1[BNMAX * BLD];  // R1 = L1^T (upper) kept for R = R2 R1
   double P[BPANEL * BLD];  // row panel of A or Q1, [row][col]
+  double rd[BNMAX];        // reciprocals of L's diagonal
   int fail_pivot;
 };
+
+// acc[s] += sum over the 32 rows of the panel of P(r, oi[s]) P(r, oj[s]) for
+// the first NS slots. A slot whose 32 pairs all lie beyond the P pairs of
+// this n is skipped by the whole warp: the FP64 pipe issues a warp
+// instruction at full cost whatever its lane mask or predicate, so the
+// branch sits outside the row loop and idle slots issue nothing.
+template <int NS>
+__device__ __forceinline__ void gram_panel_ns(const double* __restrict__ Pn, const int* oi, const int* oj,
+                                              const bool* wact, double* acc) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (wact[s]) {
+      double a = acc[s];
+#pragma unroll 8
+      for (int kk = 0; kk < BPANEL; ++kk) a = fma(Pn[kk * BLD + oi[s]], Pn[kk * BLD + oj[s]], a);
+      acc[s] = a;
+    }
+  }
+}
+
+__device__ __forceinline__ void gram_panel(int nslots, const double* Pn, const int* oi, const int* oj,
+                                           const bool* wact, double* acc) {
+  switch (nslots) {
+    case 1: gram_panel_ns<1>(Pn, oi, oj, wact, acc); break;
+    case 2: gram_panel_ns<2>(Pn, oi, oj, wact, acc); break;
+    case 3: gram_panel_ns<3>(Pn, oi, oj, wact, acc); break;
+    case 4: gram_panel_ns<4>(Pn, oi, oj, wact, acc); break;
+    case 5: gram_panel_ns<5>(Pn, oi, oj, wact, acc); break;
+    case 6: gram_panel_ns<6>(Pn, oi, oj, wact, acc); break;
+    case 7: gram_panel_ns<7>(Pn, oi, oj, wact, acc); break;
+    case 8: gram_panel_ns<8>(Pn, oi, oj, wact, acc); break;
+    default: gram_panel_ns<BS>(Pn, oi, oj, wact, acc); break;
+  }
+}
+
+// Register prefetch of a 32-row panel (all n columns): thread t holds the
+// elements e = t + BT i of the panel, e = r + 32 c. Issued before the current
+// panel's arithmetic, so the global load latency overlaps it.
+constexpr int PF = BPANEL * BNMAX / BT;  // 8
+__device__ __forceinline__ void panel_load(const double* X, int64_t ldx, int64_t m, int n, int64_t r0, double* pf) {
+#pragma unroll
+  for (int i = 0; i < PF; ++i) {
+    const int e = threadIdx.x + BT * i;
+    const int r = e % BPANEL, c = e / BPANEL;
+    pf[i] = (c < n && r0 + r < m) ? X[r0 + r + (int64_t)c * ldx] : 0.0;
+  }
+}
+__device__ __forceinline__ void panel_store(const double* pf, int n, double* P) {
+#pragma unroll
+  for (int i = 0; i < PF; ++i) {
+    const int e = threadIdx.x + BT * i;
+    const int r = e % BPANEL, c = e / BPANEL;
+    if (c < n) P[r * BLD + c] = pf[i];
+  }
+}
 
 // Right-looking Cholesky of S (n x n, lower) and inverse into T; returns the
 // first bad pivot index or -1. All threads participate.
@@ -45,23 +101,28 @@ __device__ int cholinv_smem(SmallSmem& sm, int n) {
     sm.T[j * BLD + i] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // One division per pivot (its reciprocal); the column and the inverse's
+  // row are then scaled by multiplication: on GB300 an FP64 division costs
+  // many times a multiply, and the n pivots are a serial chain.
   for (int k = 0; k < n; ++k) {
     if (t == 0) {
       const double d = sm.S[k * BLD + k];
       if ((!(d > 0.0) || !isfinite(d)) && sm.fail_pivot < 0) sm.fail_pivot = k;
-      sm.S[k * BLD + k] = sqrt(d);
+      const double l = sqrt(d);
+      sm.S[k * BLD + k] = l;
+      sm.rd[k] = 1.0 / l;
     }
     __syncthreads();
-    const double l = sm.S[k * BLD + k];
-    for (int i = k + 1 + t; i < n; i += BT) sm.S[k * BLD + i] /= l;
+    const double rl = sm.rd[k];
+    for (int i = k + 1 + t; i < n; i += BT) sm.S[k * BLD + i] *= rl;
     __syncthreads();
     for (int j = k + 1 + tx; j < n; j += 16)
       for (int i = j + ty; i < n; i += 16) sm.S[j * BLD + i] = fma(-sm.S[k * BLD + i], sm.S[k * BLD + j], sm.S[j * BLD + i]);
     __syncthreads();
   }
   for (int k = 0; k < n; ++k) {
-    const double lkk = sm.S[k * BLD + k];
-    for (int j = t; j <= k; j += BT) sm.T[j * BLD + k] /= lkk;
+    const double rkk = sm.rd[k];
+    for (int j = t; j <= k; j += BT) sm.T[j * BLD + k] *= rkk;
     __syncthreads();
     for (int j = tx; j <= k; j += 16)
       for (int i = k + 1 + ty; i < n; i += 16) sm.T[j * BLD + i] = fma(-sm.S[k * BLD + i], sm.T[j * BLD + k], sm.T[j * BLD + i]);
@@ -103,6 +164,9 @@ __global__ void __launch_bounds__(BT, 1) k_cqr2_small_batched(const BatchProblem
       }
     }
     const int nslots = (P + BT - 1) / BT;
+    bool wact[BS];  // slot s of this warp holds at least one real pair
+#pragma unroll
+    for (int s = 0; s < BS; ++s) wact[s] = (t & ~31) + s * BT < P;
     int fail_pass = 0, fail_pivot = -1;
     for (int pass = 1; pass <= 2; ++pass) {
       const double* X = pass == 1 ? pb.A : pb.Q;
@@ -112,19 +176,13 @@ __global__ void __launch_bounds__(BT, 1) k_cqr2_small_batched(const BatchProblem
       for (int s = 0; s < BS; ++s) acc[s] = 0.0;
       if (pass == 1) {
         // W1 = A^T A
+        double pf[PF];
+        panel_load(X, ldx, m, n, 0, pf);
         for (int64_t r0 = 0; r0 < m; r0 += BPANEL) {
-          for (int e = t; e < BPANEL * n; e += BT) {
-            const int r = e % BPANEL, c = e / BPANEL;
-            sm.P[r * BLD + c] = (r0 + r < m) ? X[r0 + r + (int64_t)c * ldx] : 0.0;
-          }
+          panel_store(pf, n, sm.P);
           __syncthreads();
-#pragma unroll 4
-          for (int kk = 0; kk < BPANEL; ++kk) {
-            const double* row = sm.P + kk * BLD;
-#pragma unroll
-            for (int s = 0; s < BS; ++s)
-              if (s < nslots) acc[s] = fma(row[oi[s]], row[oj[s]], acc[s]);
-          }
+          if (r0 + BPANEL < m) panel_load(X, ldx, m, n, r0 + BPANEL, pf);
+          gram_panel(nslots, sm.P, oi, oj, wact, acc);
           __syncthreads();
         }
       }
@@ -164,12 +222,15 @@ __global__ void __launch_bounds__(BT, 1) k_cqr2_small_batched(const BatchProblem
       double cacc[BNMAX / 8];
 #pragma unroll
       for (int q = 0; q < BNMAX / 8; ++q) cacc[q] = 0.0;
+      double pf[PF];
+      panel_load(X, ldx, m, n, 0, pf);
       for (int64_t r0 = 0; r0 < m; r0 += BPANEL) {
-        for (int e = t; e < BPANEL * n; e += BT) {
-          const int r = e % BPANEL, c = e / BPANEL;
-          sm.P[r * BLD + c] = (r0 + r < m) ? X[r0 + r + (int64_t)c * ldx] : 0.0;
-        }
+        panel_store(pf, n, sm.P);
         __syncthreads();
+        // The next panel's loads go out now. In pass 2, X is Q itself: the
+        // next panel's rows are read before this iteration writes (only) the
+        // current panel's rows.
+        if (r0 + BPANEL < m) panel_load(X, ldx, m, n, r0 + BPANEL, pf);
         // each warp owns columns j = warp, warp+8, ...; lane owns row r0+lane
         double qv[BNMAX / 8];
 #pragma unroll
@@ -193,15 +254,7 @@ __global__ void __launch_bounds__(BT, 1) k_cqr2_small_batched(const BatchProblem
           }
         }
         __syncthreads();
-        if (pass == 1) {
-#pragma unroll 4
-          for (int kk = 0; kk < BPANEL; ++kk) {
-            const double* row = sm.P + kk * BLD;
-#pragma unroll
-            for (int s = 0; s < BS; ++s)
-              if (s < nslots) gacc[s] = fma(row[oi[s]], row[oj[s]], gacc[s]);
-          }
-        }
+        if (pass == 1) gram_panel(nslots, sm.P, oi, oj, wact, gacc);
         __syncthreads();
       }
       if (with_c) {
