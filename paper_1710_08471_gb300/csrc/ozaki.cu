@@ -420,9 +420,9 @@ __device__ __forceinline__ OzItem oz_item(const OzParams& p, int64_t it) {
   return w;
 }
 
-// First work item of CTA b of G (CTA G gives the end). Each CTA takes a
-// contiguous range of items. Gram items cost the same, so the ranges hold
-// equal counts. A Q-form item costs its K-blocks plus a fixed epilogue (model:
+// First work item of CTA b of G (CTA G gives the end) when each CTA takes a
+// contiguous range of items (the Q-form; the Gram deals its equal-cost items
+// round-robin instead). A Q-form item costs its K-blocks plus a fixed epilogue (model:
 // nk + 1); the ranges split the total cost evenly, so that no CTA is left with
 // only the widest tiles.
 template <int MODE, int BN>
@@ -489,7 +489,13 @@ __device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* X, long l
   }
 }
 
-// Persistent: CTA b takes the items of its range in order. The producer, the
+// Item number of a CTA's it-th item (see it_begin below).
+template <int MODE>
+__device__ __forceinline__ int64_t oz_item_id(int64_t it) {
+  return MODE == OZ_GRAM ? (int64_t)blockIdx.x + it * gridDim.x : it;
+}
+
+// Persistent: CTA b takes its items in order. The producer, the
 // MMA issuer and the epilogue walk the same item sequence with running
 // counters (K-blocks, A slices, chunks), so the mbarrier phases continue
 // across items. Group g of chunk c lives in accumulator buffer c % NBUF; the
@@ -544,8 +550,15 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
-  const int64_t it_begin = oz_range_begin<MODE, BN>(p, blockIdx.x, gridDim.x);
-  const int64_t it_end = oz_range_begin<MODE, BN>(p, blockIdx.x + 1, gridDim.x);
+  // Gram items are dealt round-robin (the CTA's k-th item is blockIdx.x + k
+  // gridDim.x): the CTAs running side by side then hold the tiles of the same
+  // row ranges and read each slice K-block from DRAM once between them, the
+  // others finding it in L2. Q-form items go in cost-balanced contiguous
+  // ranges (oz_range_begin).
+  const int64_t it_begin = MODE == OZ_GRAM ? 0 : oz_range_begin<MODE, BN>(p, blockIdx.x, gridDim.x);
+  const int64_t it_end = MODE == OZ_GRAM
+                             ? (p.nitems > (int64_t)blockIdx.x ? (p.nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0)
+                             : oz_range_begin<MODE, BN>(p, blockIdx.x + 1, gridDim.x);
 
   // Ring positions run on across items: A slot and its phase parity, B buffer
   // and its parity. The single issuing threads keep their loops short (no
@@ -561,7 +574,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       for (int i = 0; i < NA; ++i) alast[i] = -1;
       blast[0] = blast[1] = -1;
       for (int64_t it = it_begin; it < it_end && ok; ++it) {
-        const OzItem w = oz_item<MODE, BN>(p, it);
+        const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
         for (int kb = 0; kb < w.nk; ++kb) {
           const int k0 = (int)(w.kbase + (int64_t)kb * OZ_BK);
           if (bwrapped && !(ok = mbar_wait(&bempty[buf], bph ^ 1u, p.st))) break;
@@ -620,7 +633,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       int64_t gc = 0;            // chunks issued
       int64_t used0 = 0, used1 = 0;  // two epilogue groups: chunks issued into buffer 0, 1
       for (int64_t it = it_begin; it < it_end && ok; ++it) {
-        const OzItem w = oz_item<MODE, BN>(p, it);
+        const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
         const int par_it = (int)((it - it_begin) & 1);
         for (int kb = 0; kb < w.nk; ++kb) {
           const bool first = (kb & 1) == 0;  // the chunk's first K-block overwrites its groups
@@ -695,7 +708,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
     int64_t gc = 0;  // chunks drained (by this group)
     for (int64_t it = it_begin; it < it_end && ok; ++it) {
       if (NGRP == 2 && (int)((it - it_begin) & 1) != grp) continue;
-      const OzItem w = oz_item<MODE, BN>(p, it);
+      const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
       const int nchunks = (w.nk + 1) >> 1;
       long long X[CPT], Y[CPT];
 #pragma unroll
