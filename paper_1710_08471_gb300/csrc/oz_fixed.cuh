@@ -92,6 +92,18 @@ OZ_HD double oz_xy_to_double(long long X, long long Y, int E) {
   return oz_fixed_to_double(hi, lo, E);
 }
 
+#if defined(__CUDA_ARCH__)
+// The exact routine as an out-of-line call for the fast routine's rare
+// subnormal case: inlined at every output it would crowd the instruction
+// cache of the epilogue loop with code that almost never runs.
+static __device__ __noinline__ double oz_xy_to_double_cold(long long X, long long Y, int E) {
+  return oz_xy_to_double(X, Y, E);
+}
+#define OZ_XY_COLD oz_xy_to_double_cold
+#else
+#define OZ_XY_COLD oz_xy_to_double
+#endif
+
 // Faster conversion of T = X 2^24 + Y (|X| < 2^61, |Y| < 2^55) to within one
 // ulp of T 2^E: scale T by 2^-sh so that it fits 62 bits (the bits of Y that
 // fall off are below 2^-61 of it), then round that int64 to nearest.
@@ -108,7 +120,7 @@ OZ_HD double oz_xy_to_double_fast(long long X, long long Y, int E) {
   unsigned long long mant = u >> 11;
   const unsigned long long rb = (u >> 10) & 1ull, st = (u & 0x3FFull) != 0 ? 1ull : 0ull;
   const int biased = 63 - lz + E + sh + 1023;
-  if (biased < 1) return oz_xy_to_double(X, Y, E);  // subnormal: rare, exact path
+  if (biased < 1) return OZ_XY_COLD(X, Y, E);  // subnormal: rare, exact path
   mant += rb & (st | (mant & 1ull));
   unsigned long long bits = ((unsigned long long)(biased - 1) << 52) + mant;
   if (biased > 2046) bits = 0x7FF0000000000000ull;

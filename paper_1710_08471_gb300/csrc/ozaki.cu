@@ -495,6 +495,37 @@ __device__ __forceinline__ int64_t oz_item_id(int64_t it) {
   return MODE == OZ_GRAM ? (int64_t)blockIdx.x + it * gridDim.x : it;
 }
 
+// Walks a CTA's items. The Q-form's items are consecutive, so the row tile
+// and column tile advance by a counter instead of a 64-bit division per item
+// (which the single MMA-issuing thread would pay between items).
+template <int MODE, int BN>
+struct OzCursor {
+  int64_t rt = 0;  // Q-form: row tile
+  int jt = 0;      // Q-form: column tile
+  __device__ __forceinline__ void init(const OzParams& p, int64_t it0) {
+    if (MODE == OZ_QFORM) {
+      rt = it0 / p.ntile_j;
+      jt = (int)(it0 - rt * p.ntile_j);
+    }
+  }
+  __device__ __forceinline__ void next(const OzParams& p) {
+    if (MODE == OZ_QFORM && ++jt == p.ntile_j) {
+      jt = 0;
+      ++rt;
+    }
+  }
+  __device__ __forceinline__ OzItem item(const OzParams& p, int64_t it) const {
+    if (MODE == OZ_GRAM) return oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
+    OzItem w;
+    w.j0 = (int64_t)BN * jt;
+    w.i0 = (int64_t)OZ_BM * rt;
+    w.kbase = 0;
+    w.split = 0;
+    w.nk = oz_qform_nk<BN>(w.j0, p.n);
+    return w;
+  }
+};
+
 // Persistent: CTA b takes its items in order. The producer, the
 // MMA issuer and the epilogue walk the same item sequence with running
 // counters (K-blocks, A slices, chunks), so the mbarrier phases continue
@@ -573,8 +604,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       int alast[NA], blast[2];                   // parity of each slot's last fill (-1: none)
       for (int i = 0; i < NA; ++i) alast[i] = -1;
       blast[0] = blast[1] = -1;
-      for (int64_t it = it_begin; it < it_end && ok; ++it) {
-        const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
+      OzCursor<MODE, BN> cur;
+      cur.init(p, it_begin);
+      for (int64_t it = it_begin; it < it_end && ok; ++it, cur.next(p)) {
+        const OzItem w = cur.item(p, it);
         for (int kb = 0; kb < w.nk; ++kb) {
           const int k0 = (int)(w.kbase + (int64_t)kb * OZ_BK);
           if (bwrapped && !(ok = mbar_wait(&bempty[buf], bph ^ 1u, p.st))) break;
@@ -632,8 +665,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       uint32_t aph = 0, bph = 0;
       int64_t gc = 0;            // chunks issued
       int64_t used0 = 0, used1 = 0;  // two epilogue groups: chunks issued into buffer 0, 1
-      for (int64_t it = it_begin; it < it_end && ok; ++it) {
-        const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
+      OzCursor<MODE, BN> cur;
+      cur.init(p, it_begin);
+      for (int64_t it = it_begin; it < it_end && ok; ++it, cur.next(p)) {
+        const OzItem w = cur.item(p, it);
         const int par_it = (int)((it - it_begin) & 1);
         for (int kb = 0; kb < w.nk; ++kb) {
           const bool first = (kb & 1) == 0;  // the chunk's first K-block overwrites its groups
@@ -706,9 +741,11 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
     const int cs = (ew % (EPI / NGRP)) >> 2;            // column slice of each accumulator
     bool ok = true;
     int64_t gc = 0;  // chunks drained (by this group)
-    for (int64_t it = it_begin; it < it_end && ok; ++it) {
+    OzCursor<MODE, BN> cur;
+    cur.init(p, it_begin);
+    for (int64_t it = it_begin; it < it_end && ok; ++it, cur.next(p)) {
       if (NGRP == 2 && (int)((it - it_begin) & 1) != grp) continue;
-      const OzItem w = oz_item<MODE, BN>(p, oz_item_id<MODE>(it));
+      const OzItem w = cur.item(p, it);
       const int nchunks = (w.nk + 1) >> 1;
       long long X[CPT], Y[CPT];
 #pragma unroll
@@ -716,6 +753,16 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       const int64_t row = w.i0 + q4 * 32 + lane;
       const int64_t nrow = MODE == OZ_GRAM ? p.n : p.m;
       const int ea = 0;  // Q-form: X's column exponents live in R^-1's slices
+      // Q-form: the output columns' exponents, loaded now so that the loads
+      // overlap the drains (the Gram converts once per many chunks and keeps
+      // its registers for the accumulators)
+      constexpr int NEB = MODE == OZ_QFORM ? CPT : 1;
+      int eb[NEB];
+#pragma unroll
+      for (int cc = 0; cc < NEB; ++cc) {
+        const int64_t col = w.j0 + cs * CPT + cc;
+        eb[cc] = (MODE == OZ_QFORM && col < p.n) ? p.eB[col] : 0;
+      }
       for (int c = 0; c < nchunks && ok; ++c, ++gc) {
         const int ab = NGRP == 2 ? grp : (int)(gc % NBUF);
         const uint32_t par = (uint32_t)((NGRP == 2 ? gc : gc / NBUF) & 1);
@@ -749,7 +796,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
         for (int cc = 0; cc < CPT; ++cc) {
           const int64_t col = w.j0 + cs * CPT + cc;
           if (col < p.n) {
-            const int e2 = p.eB[col];
+            const int e2 = MODE == OZ_QFORM ? eb[cc < NEB ? cc : 0] : p.eB[col];
             // Gram: exact rounding; Q-form: within one ulp (far below its
             // truncation error), with a shorter integer sequence
             out[row + col * ld] = (ea2 >= EXP_NONFINITE || e2 >= EXP_NONFINITE)
