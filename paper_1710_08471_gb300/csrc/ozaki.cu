@@ -83,49 +83,55 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int S) {
   return (b >> 63) ? -v : v;
 }
 
-// BF16 bits of a small integer |d| <= 2^8: placing d in the low mantissa
+// FP32 bits of a small integer |d| <= 2^8: placing d in the low mantissa
 // bits of 1.5 * 2^23 and subtracting 1.5 * 2^23 gives d exactly in FP32 (one
 // integer add, one FP32 add); with at most 8 significant bits its low 16 bits
 // are zero, so the top half is the exact BF16 value.
-__device__ __forceinline__ unsigned small_int_to_bf16(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
+__device__ __forceinline__ unsigned small_int_f32bits(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
 }
 
-// The S digits of x (shared exponent e) as BF16 bits, most significant first.
+// The S balanced base-256 digits of x (shared exponent e), most significant
+// first, as FP32 bit patterns whose top halves are the BF16 digits. With v
+// the fixed-point value and B = 128 in each of the S - 1 low bytes, the low
+// digits are the bytes of v + B minus 128 and the top digit is (v + B)
+// shifted down arithmetically: the same digits as peeling the low byte off
+// one at a time (signed, then v = (v - d) / 256), without the serial chain.
 template <int S>
-__device__ __forceinline__ void digits_bf16(double x, int e, unsigned (&out)[S]) {
-  long long v = to_fixed(x, e, S);
+__device__ __forceinline__ void digits_f32bits(double x, int e, unsigned (&out)[S]) {
+  constexpr unsigned long long B = ((1ull << (8 * (S - 1))) - 1) / 255 * 128;
+  const unsigned long long u = (unsigned long long)to_fixed(x, e, S) + B;
+  const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
 #pragma unroll
-  for (int s = S - 1; s >= 1; --s) {
-    const int lo = (int)(signed char)(v & 0xFF);
-    out[s] = small_int_to_bf16(lo);
-    v = (v - lo) >> 8;
+  for (int i = 0; i < S - 1; ++i) {
+    const unsigned byte = ((i < 4 ? lo : hi) >> (8 * (i & 3))) & 0xFFu;
+    out[S - 1 - i] = small_int_f32bits((int)byte - 128);
   }
-  out[0] = small_int_to_bf16((int)v);
+  out[0] = small_int_f32bits((int)((long long)u >> (8 * (S - 1))));
 }
 
 // Writes the S digits of x (with shared exponent e) as BF16 to out[s * stride].
 template <int S>
 __device__ __forceinline__ void write_digits(double x, int e, unsigned short* out, size_t stride) {
   unsigned d[S];
-  digits_bf16<S>(x, e, d);
+  digits_f32bits<S>(x, e, d);
 #pragma unroll
-  for (int s = 0; s < S; ++s) out[(size_t)s * stride] = (unsigned short)d[s];
+  for (int s = 0; s < S; ++s) out[(size_t)s * stride] = (unsigned short)(d[s] >> 16);
 }
 
-// Digits of four consecutive entries, written as one 8-byte store per slice.
+// Digits of four consecutive entries, written as one 8-byte store per slice
+// (the BF16 halves of two FP32 patterns joined by one byte permute).
 template <int S>
 __device__ __forceinline__ void write_digits4(const double (&x)[4], const int (&e)[4], unsigned short* out,
                                               size_t stride) {
   unsigned d[4][S];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) digits_bf16<S>(x[q], e[q], d[q]);
+  for (int q = 0; q < 4; ++q) digits_f32bits<S>(x[q], e[q], d[q]);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     uint2 w;
-    w.x = d[0][s] | (d[1][s] << 16);
-    w.y = d[2][s] | (d[3][s] << 16);
+    w.x = __byte_perm(d[0][s], d[1][s], 0x7632);
+    w.y = __byte_perm(d[2][s], d[3][s], 0x7632);
     *reinterpret_cast<uint2*>(out + (size_t)s * stride) = w;
   }
 }
