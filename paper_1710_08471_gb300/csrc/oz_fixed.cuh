@@ -1,7 +1,10 @@
-// Fixed-point accumulator -> FP64 conversion of the split-precision path,
-// with integer operations only (GB300's FP64 pipe is far too slow even for
-// conversions). Host-compilable, so the rounding can be checked on the CPU
-// against exact rational arithmetic.
+// Integer arithmetic of the split-precision path, host-compilable so that it
+// can be checked on the CPU against exact rational arithmetic:
+// - slicing: an FP64 entry x with shared exponent e (|x| < 2^e) becomes the
+//   fixed-point integer v = round(x 2^(7 + 8 (S - 1) - e)) and then S
+//   balanced base-256 digits, v = sum_s d_s 256^(S - 1 - s);
+// - recombination: the fixed-point accumulators back to FP64, with integer
+//   operations only (GB300's FP64 pipe is far too slow even for conversions).
 #pragma once
 
 #include <stdint.h>
@@ -14,6 +17,64 @@
 #endif
 
 namespace cqr2 {
+
+constexpr int OZ_EXP_NONFINITE = 1 << 20;  // exponent sentinel: a non-finite entry was seen
+
+OZ_HD long long oz_double_bits(double x) {
+#if defined(__CUDA_ARCH__)
+  return __double_as_longlong(x);
+#else
+  long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+
+// v = x 2^(7 + 8 (S - 1) - e), rounded half away from zero, for |x| < 2^e:
+// |v| < 2^(7 + 8 (S - 1)). Zero for a non-finite x or exponent.
+OZ_HD long long oz_to_fixed(double x, int e, int S) {
+  const unsigned long long b = (unsigned long long)oz_double_bits(x);
+  int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long mant = b & ((1ull << 52) - 1);
+  if (ex == 0) {
+    if (mant == 0) return 0;
+    ex = 1;
+  } else {
+    mant |= 1ull << 52;
+  }
+  if (e >= OZ_EXP_NONFINITE || ex == 0x7FF) return 0;
+  const int sh = ex - 1075 + 7 + 8 * (S - 1) - e;  // < 8S - 53 because |x| < 2^e
+  long long v;
+  if (sh >= 0) {
+    v = (long long)(mant << sh);
+  } else if (sh > -63) {
+    v = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
+  } else {
+    v = 0;
+  }
+  return (b >> 63) ? -v : v;
+}
+
+// Balanced base-256 digits of v, most significant first: d[1..S-1] in
+// [-128, 127] and v = sum_s d[s] 256^(S - 1 - s). With B = 128 in each of the
+// S - 1 low bytes, the low digits are the bytes of v + B minus 128 and the
+// top digit is v + B shifted down arithmetically -- the same digits as
+// peeling the signed low byte off one at a time (d = sext(v mod 256), v =
+// (v - d) / 256), without that serial chain.
+template <int S>
+OZ_HD void oz_balanced_digits(long long v, int (&d)[S]) {
+  constexpr unsigned long long B = ((1ull << (8 * (S - 1))) - 1) / 255 * 128;
+  const unsigned long long u = (unsigned long long)v + B;
+  const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+  for (int i = 0; i < S - 1; ++i) {
+    const unsigned byte = ((i < 4 ? lo : hi) >> (8 * (i & 3))) & 0xFFu;
+    d[S - 1 - i] = (int)byte - 128;
+  }
+  d[0] = (int)((long long)u >> (8 * (S - 1)));
+}
 
 OZ_HD int oz_clz64(unsigned long long x) {
 #if defined(__CUDA_ARCH__)

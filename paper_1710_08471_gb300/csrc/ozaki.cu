@@ -46,7 +46,7 @@ namespace {
 
 constexpr int OZ_BK = 64;          // contraction per K-block (128-byte rows)
 constexpr int OZ_BM = 128;         // tile rows
-constexpr int EXP_NONFINITE = 1 << 20;  // exponent sentinel: a non-finite entry was seen
+constexpr int EXP_NONFINITE = OZ_EXP_NONFINITE;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
 // ------------------------------------------------------------ digits
@@ -60,29 +60,6 @@ __device__ __forceinline__ int exp_from_bits(unsigned long long absbits) {
   return ex - 1022;
 }
 
-__device__ __forceinline__ long long to_fixed(double x, int e, int S) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  int ex = (int)((b >> 52) & 0x7FF);
-  unsigned long long mant = b & ((1ull << 52) - 1);
-  if (ex == 0) {
-    if (mant == 0) return 0;
-    ex = 1;
-  } else {
-    mant |= 1ull << 52;
-  }
-  if (e >= EXP_NONFINITE || ex == 0x7FF) return 0;
-  const int sh = ex - 1075 + 7 + 8 * (S - 1) - e;  // < 8S - 53 because |x| < 2^e
-  long long v;
-  if (sh >= 0) {
-    v = (long long)(mant << sh);
-  } else if (sh > -63) {
-    v = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
-  } else {
-    v = 0;
-  }
-  return (b >> 63) ? -v : v;
-}
-
 // FP32 bits of a small integer |d| <= 2^8: placing d in the low mantissa
 // bits of 1.5 * 2^23 and subtracting 1.5 * 2^23 gives d exactly in FP32 (one
 // integer add, one FP32 add); with at most 8 significant bits its low 16 bits
@@ -92,22 +69,13 @@ __device__ __forceinline__ unsigned small_int_f32bits(int d) {
 }
 
 // The S balanced base-256 digits of x (shared exponent e), most significant
-// first, as FP32 bit patterns whose top halves are the BF16 digits. With v
-// the fixed-point value and B = 128 in each of the S - 1 low bytes, the low
-// digits are the bytes of v + B minus 128 and the top digit is (v + B)
-// shifted down arithmetically: the same digits as peeling the low byte off
-// one at a time (signed, then v = (v - d) / 256), without the serial chain.
+// first, as FP32 bit patterns whose top halves are the BF16 digits.
 template <int S>
 __device__ __forceinline__ void digits_f32bits(double x, int e, unsigned (&out)[S]) {
-  constexpr unsigned long long B = ((1ull << (8 * (S - 1))) - 1) / 255 * 128;
-  const unsigned long long u = (unsigned long long)to_fixed(x, e, S) + B;
-  const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
+  int d[S];
+  oz_balanced_digits<S>(oz_to_fixed(x, e, S), d);
 #pragma unroll
-  for (int i = 0; i < S - 1; ++i) {
-    const unsigned byte = ((i < 4 ? lo : hi) >> (8 * (i & 3))) & 0xFFu;
-    out[S - 1 - i] = small_int_f32bits((int)byte - 128);
-  }
-  out[0] = small_int_f32bits((int)((long long)u >> (8 * (S - 1))));
+  for (int s = 0; s < S; ++s) out[s] = small_int_f32bits(d[s]);
 }
 
 // Writes the S digits of x (with shared exponent e) as BF16 to out[s * stride].

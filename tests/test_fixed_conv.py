@@ -1,4 +1,6 @@
-"""Host check of the split-precision accumulator -> FP64 conversion.
+"""Host check of the split-precision integer arithmetic: the slicing of FP64
+entries into balanced base-256 digits, and the accumulator -> FP64
+conversion.
 
 The kernel turns its two int64 fixed-point accumulators into a double with
 integer operations: exactly (hi 2^32 + lo, or X 2^24 + Y) for the Gram, and
@@ -122,3 +124,78 @@ def test_xy_fast_within_one_ulp(conv):
             assert struct.pack("<d", g) == struct.pack("<d", want), (x, y, e, g, want)
         else:
             assert abs(Fraction(g) - Fraction(t) * Fraction(2) ** e) <= Fraction(_ulp(want)), (x, y, e, g, want)
+
+
+# ---------------------------------------------------------------- slicing
+
+@pytest.fixture(scope="module")
+def slicer(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("slice") / "fixed_conv_check")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "native", "fixed_conv_check.cpp"),
+                    "-o", exe], check=True)
+
+    def run(cases):
+        lines = []
+        for x, e, S in cases:
+            bits = struct.unpack("<q", struct.pack("<d", x))[0]
+            lines.append(f"3 {bits} {S} {e}\n")
+        out = subprocess.run([exe], input="".join(lines), capture_output=True, text=True, check=True).stdout
+        res = []
+        for ln in out.strip().split("\n"):
+            w = [int(t) for t in ln.split()]
+            res.append((w[0], w[1:]))
+        return res
+
+    return run
+
+
+def _peel(v, S):
+    """Balanced base-256 digits by the definition: the signed low byte, then
+    (v - d) / 256, repeated; the rest is the top digit."""
+    d = [0] * S
+    for s in range(S - 1, 0, -1):
+        lo = v & 0xFF
+        lo = lo - 256 if lo >= 128 else lo
+        d[s] = lo
+        v = (v - lo) >> 8
+    d[0] = v
+    return d
+
+
+def test_slicing_digits(slicer):
+    """Every entry x with |x| < 2^e becomes v = x 2^(7 + 8(S-1) - e) rounded
+    to an integer (half away from zero, error <= 1/2, exact when no bits are
+    dropped), and S balanced digits with v = sum d_s 256^(S-1-s), d_s in
+    [-128, 127] below the top digit, equal to the digits peeled off one byte
+    at a time."""
+    rng = random.Random(11)
+    cases = []
+    for _ in range(6000):
+        S = rng.choice((6, 7))
+        e = rng.randint(-60, 60)
+        kind = rng.random()
+        if kind < 0.6:
+            x = rng.uniform(-1.0, 1.0) * 2.0 ** e
+        elif kind < 0.8:
+            x = rng.uniform(-1.0, 1.0) * 2.0 ** (e - rng.randint(1, 80))
+        else:  # just below 2^e, and ties in the last kept place
+            k = 7 + 8 * (S - 1) - e
+            x = (rng.choice((1, -1)) * ((1 << (7 + 8 * (S - 1))) - rng.randint(0, 3)) + rng.choice((0, 0.5))) * 2.0 ** -k
+            if abs(x) >= 2.0 ** e:
+                x = 0.0
+        cases.append((x, e, S))
+    cases += [(0.0, 0, 7), (-0.0, 3, 6), (5e-324, -1021, 7), (-2.0 ** -1030, -1025, 6)]
+    got = slicer(cases)
+    for (x, e, S), (v, d) in zip(cases, got):
+        k = 7 + 8 * (S - 1) - e
+        t = Fraction(x) * Fraction(2) ** k
+        assert abs(t) < Fraction(2) ** (7 + 8 * (S - 1)) or x == 0.0
+        assert abs(Fraction(v) - t) <= Fraction(1, 2), (x, e, S, v)
+        if t.denominator == 1:
+            assert v == t, (x, e, S, v)
+        assert sum(di * 256 ** (S - 1 - i) for i, di in enumerate(d)) == v
+        assert all(-128 <= di <= 127 for di in d[1:]) and abs(d[0]) <= 128
+        assert d == _peel(v, S), (x, e, S)
