@@ -45,7 +45,11 @@ WORKLOADS = {
     "wide512": (1 << 21, 512, 1e6, 3, "FP64 CholeskyQR2, m=2^21 n=512 (8.6 GB), kappa=1e6"),
     # profiling size: larger than L2, a few GB on the device
     "mid": (1 << 20, 128, 1e6, 1, "FP64 CholeskyQR2, m=2^20 n=128 (1.07 GB), kappa=1e6"),
+    # many small problems in one grouped launch (one step = one batch call)
+    "batch": (4096, 32, None, 5, "grouped batch: 1024 FP64 CholeskyQR2 problems, m=4096 n=32 each (1.07 GB), "
+                                 "iid N(0,1)"),
 }
+BATCH_COUNT = 1024
 
 # GB300 FP64: 2 DFMA per clock per SM (one warp instruction every 16 clocks
 # per SM partition), 152 SMs, 2 flops per FMA, at the maximum SM clock.
@@ -233,6 +237,8 @@ def bench_reference(args, ws, rank):
     m, n, kappa, seed, desc = WORKLOADS[args.workload]
     if rank != 0:
         return
+    if args.workload == "batch":
+        return bench_reference_batch(args, ws)
     rows = min(m, args.oracle_rows or (1 << 21))
     A, _ = make_input(rows, n, kappa, seed, pinned=False)
     times = []
@@ -256,6 +262,148 @@ def bench_reference(args, ws, rank):
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def batch_config(args, ws: int) -> dict:
+    m, n, kappa, seed, desc = WORKLOADS["batch"]
+    return {"workload": desc, "m": m, "n": n, "count": BATCH_COUNT, "precision": "fp64", "variant": "grouped",
+            "parallelism": f"replicas{ws}" if ws > 1 else "single",
+            "l2": f"inputs {BATCH_COUNT * m * n * 8 / 1e9:.2f} GB > 129 MB L2 (no flush)"}
+
+
+def bench_reference_batch(args, ws):
+    """The oracle on a bounded sample of the batch's problems."""
+    import oracle
+
+    m, n, kappa, seed, desc = WORKLOADS["batch"]
+    count = min(BATCH_COUNT, args.oracle_rows or 64)  # problems per step
+    A = synth.make_matrix(count * m, n, kappa, seed)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for p in range(count):
+            oracle.cqr2(np.asfortranarray(A[p * m:(p + 1) * m]))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    val = count * nominal_flops(m, n) / (ms * 1e-3) / 1e12
+    sample = f"{count} of the {BATCH_COUNT} problems per step ({desc}); numpy FP64 oracle, one problem at a time"
+    line = {
+        "impl": "reference", "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": val, "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(batch_config(args, ws), sampled_problems=count),
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_batch(args, ws, rank, local):
+    """One step = one cqr2_batch_factor call over BATCH_COUNT problems, all
+    routed to the persistent grouped kernel, replayed from a captured graph."""
+    import torch
+
+    import paper_1710_08471_gb300 as cq
+
+    m, n, kappa, seed, desc = WORKLOADS["batch"]
+    count = BATCH_COUNT
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hA, hA_t = make_input(count * m, n, kappa, seed + 1000 * rank, pinned=True)
+    A = cq.empty_colmajor(count * m, n, device=dev)
+    A.t().copy_(hA_t.to(dev, non_blocking=True))
+    Q = cq.empty_colmajor(count * m, n, device=dev)
+    R = cq.empty_colmajor(n, count * n, device=dev)
+    probs = [(A[i * m:(i + 1) * m], Q[i * m:(i + 1) * m], R[:, i * n:(i + 1) * n]) for i in range(count)]
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    batch = cq.Batch(count, stream=stream, graph=True, small_work_limit=m * n * n)
+    desc_arr = batch.descriptors(probs)
+    infos = batch.factor(desc_arr)
+    if any(i.status != 0 for i in infos):
+        raise SystemExit("batch factorization failed")
+    for _ in range(args.warmup):
+        batch.factor(desc_arr, sync=False)
+    batch.info()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = cq.cqr2_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.factor(desc_arr, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = cq.cqr2_launch_count() - l0
+    barrier(ws)
+    ms_local = e0.elapsed_time(e1) / args.steps
+    flops = count * nominal_flops(m, n)
+    value, ms_step = replica_throughput(ws, flops, ms_local)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    fp64_peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
+    achieved = flops / (ms_local * 1e-3) / 1e12
+    out = {
+        "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batch_config(args, ws),
+        "gpu_launches": launches,
+        "qr_per_s": ws * count / (ms_step * 1e-3),
+        "roofline": {"bound": "alu", "kernel": "k_cqr2_small_batched", "stage": "batch", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": NCU_TRAFFIC.get(f"k_cqr2_small_batched@batch@{src_sha('batched.cu')}"),
+                     "peak_note": f"derived FP64 DFMA peak: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 "
+                                  f"flops x {sm_max:.0f} MHz; work = nominal flops of every problem"},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.quick:
+        import oracle
+
+        # errors on a sample of problems against the oracle, and the CPU baseline
+        sample = list(range(0, count, count // 8))
+        errs = []
+        t_cpu = 0.0
+        for i in sample:
+            Ai = np.asfortranarray(hA[i * m:(i + 1) * m])
+            Qi = probs[i][1].cpu().numpy()
+            Ri = probs[i][2].cpu().numpy()
+            t0 = time.perf_counter()
+            Qo, Ro = oracle.cqr2(Ai)
+            t_cpu += time.perf_counter() - t0
+            errs.append({"orthogonality": oracle.orthogonality(Qi), "residual": oracle.residual(Ai, Qi, Ri),
+                         "R_rel_vs_oracle": oracle.rel_error(np.asfortranarray(Ri), Ro)})
+        out["errors"] = {k: max(e[k] for e in errs) for k in errs[0]}
+        out["errors"]["problems_checked"] = len(sample)
+        out["cpu_baseline"] = {"value": len(sample) * nominal_flops(m, n) / t_cpu / 1e12, "unit": "TFLOP/s",
+                               "cores": cpu_cores(), "kind": "oracle", "seconds": t_cpu,
+                               "sample": f"{len(sample)} of the {count} problems ({desc}); numpy FP64 oracle"}
+        # end to end: every problem's A in from pinned host memory, Q and R
+        # back, around the same batch call
+        hQ_t = torch.empty((n, count * m), dtype=torch.float64, pin_memory=True)
+        hR_t = torch.empty((count * n, n), dtype=torch.float64, pin_memory=True)
+        times = []
+        for _ in range(max(2, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                A.t().copy_(hA_t, non_blocking=True)
+                batch.factor(desc_arr, sync=False)
+                hQ_t.copy_(Q.t(), non_blocking=True)
+                hR_t.copy_(R.t(), non_blocking=True)
+            stream.synchronize()
+            times.append(time.perf_counter() - t0)
+        batch.info()
+        e2e_ms = 1e3 * statistics.median(times)
+        out["e2e"] = {"value": flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                      "h2d_bytes_per_step": count * m * n * 8, "d2h_bytes_per_step": count * (m * n + n * n) * 8,
+                      "api": "cqr2_batch_factor with pinned host copies on the batch stream"}
+    batch.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 PRECISIONS = {"fp64": 0, "ozaki": 1, "ozaki6": 2}
@@ -506,7 +654,10 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     try:
-        bench_ours(args, ws, rank, local)
+        if args.workload == "batch":
+            bench_batch(args, ws, rank, local)
+        else:
+            bench_ours(args, ws, rank, local)
     finally:
         if ws > 1:
             import torch.distributed as dist

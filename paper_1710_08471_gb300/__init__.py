@@ -286,11 +286,16 @@ class Batch:
         self.handle = h
         self.max_count = int(max_count)
 
-    def factor(self, problems, sync: bool = True):
-        """problems: list of (A, Q, R) or, for least squares, (A, Q, R, b, x)
-        with column-major CUDA float64 matrices and contiguous vectors b (m)
-        and x (n). Returns a list of Info (sync=True) or None (then info()
-        reports the outcomes)."""
+    class Descriptors:
+        """A problem list's C descriptor array (see Batch.descriptors)."""
+
+        def __init__(self, arr, count):
+            self.arr, self.count = arr, count
+
+    @staticmethod
+    def descriptors(problems):
+        """The C descriptor array of a problem list, reusable across factor()
+        calls (the tensors must stay alive)."""
         k = len(problems)
         arr = (N.Problem * max(k, 1))()
         for i, pr in enumerate(problems):
@@ -303,6 +308,15 @@ class Batch:
             if len(pr) > 3:
                 bp, xp = _vec(pr[3], m, "b"), _vec(pr[4], n, "x")
             arr[i] = N.Problem(m, n, a, lda, q, ldq, r, ldr, bp, xp)
+        return Batch.Descriptors(arr, k)
+
+    def factor(self, problems, sync: bool = True):
+        """problems: list of (A, Q, R) or, for least squares, (A, Q, R, b, x)
+        with column-major CUDA float64 matrices and contiguous vectors b (m)
+        and x (n), or the result of descriptors(). Returns a list of Info
+        (sync=True) or None (then info() reports the outcomes)."""
+        d = problems if isinstance(problems, Batch.Descriptors) else self.descriptors(problems)
+        arr, k = d.arr, d.count
         infos = (Info * max(k, 1))() if sync else None
         st = N.load().cqr2_batch_factor(self.handle, arr, k, infos)
         self._last = k

@@ -49,3 +49,12 @@ def test_reference_and_gpu_arms_share_the_config():
     cfg = bench.workload_config(A, 1)
     assert cfg["m"] == 1 << 21 and cfg["n"] == 512 and cfg["variant"] == "plain"  # fusion is FP64-only
     assert bench.stage_work(1 << 20, 128, "fp64", True)["qform1"] == 2 * (1 << 20) * 128 * 129
+
+
+def test_reference_arm_batch_workload():
+    d = _line("--impl", "reference", "--steps", "1", "--warmup", "0", "--oracle-rows", "4", "--workload", "batch")
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "TFLOP/s"
+    cfg = d["config"]
+    assert cfg["m"] == 4096 and cfg["n"] == 32 and cfg["count"] == 1024 and cfg["sampled_problems"] == 4
+    assert cfg["variant"] == "grouped" and cfg["precision"] == "fp64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and "4 of the 1024 problems" in d["cpu_baseline"]["sample"]
