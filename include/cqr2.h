@@ -378,7 +378,8 @@ cqr2_status_t cqr2_plan_stage_times(cqr2_plan_t plan, double* ms, int64_t* count
 /* Static name of a stage ("gram1", "qform2", ...). */
 const char* cqr2_stage_name(int32_t stage);
 
-/* Number of CUDA kernels this library has launched in this process. */
+/* Number of CUDA kernels this library has launched in this process (a CUDA
+ * graph replay adds the kernels the graph runs). */
 int64_t cqr2_launch_count(void);
 
 /* Human-readable name of a status code (static string). */

@@ -14,6 +14,7 @@ using namespace cqr2;
 namespace cqr2 {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace cqr2
 
@@ -90,6 +91,7 @@ struct cqr2_plan_st {
     void* R;
     int64_t lda, ldq, ldr, m;
   } gkey{};
+  int64_t g_kernels = 0;  // kernels in the captured graph
   // per-stage CUDA-event timing
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -635,7 +637,9 @@ cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64
       p->gexec = nullptr;
       p->graph = nullptr;
       TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+      const int64_t l0 = launch_count();
       r = factor_any(p, dA, lda, dQ, ldq, dR, ldr);
+      p->g_kernels = launch_count() - l0;  // counted once here, and again at every replay
       cudaGraph_t g = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
       if (r != CQR2_OK || ce != cudaSuccess) {
@@ -656,6 +660,7 @@ cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64
       p->gkey.ldr = ldr;
       p->gkey.m = m;
     }
+    if (same) count_launches(p->g_kernels);
     TRY(cudaGraphLaunch(p->gexec, p->stream));
   } else if ((r = factor_any(p, dA, lda, dQ, ldq, dR, ldr)) != CQR2_OK) {
     return r;

@@ -58,6 +58,7 @@ struct cqr2_batch_st {
   cudaGraphExec_t gexec = nullptr;             // captured for gkey, if any
   std::vector<int> g_small, g_used;            // its outcome locations
   int64_t replays = 0;
+  int64_t g_kernels = 0;                       // kernels in the captured graph
 };
 
 namespace {
@@ -193,7 +194,9 @@ cqr2_status_t batch_enqueue_graph(cqr2_batch_t b, const cqr2_problem_t* problems
   }
   if (!b->gexec) {
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CQR2_ERR_CUDA;
+    const int64_t l0 = launch_count();
     const cqr2_status_t r = batch_enqueue(b, problems, count);
+    b->g_kernels = launch_count() - l0;
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
     if (r != CQR2_OK || ce != cudaSuccess || cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
@@ -210,6 +213,7 @@ cqr2_status_t batch_enqueue_graph(cqr2_batch_t b, const cqr2_problem_t* problems
     b->last_small = b->g_small;
     b->last_used = b->g_used;
     ++b->replays;
+    count_launches(b->g_kernels);
   }
   return cudaGraphLaunch(b->gexec, b->stream) == cudaSuccess ? CQR2_OK : CQR2_ERR_CUDA;
 }

@@ -13,6 +13,7 @@ namespace cqr2 {
 
 // Process-wide count of kernel launches issued by this library.
 void count_launch();
+void count_launches(int64_t k);  // a graph replay: the kernels it runs
 int64_t launch_count();
 
 // ---------------------------------------------------------------- Gram

@@ -87,10 +87,14 @@ def test_graph_replay_matches_direct(cq, prec):
     with cq.Plan(m, n, precision=prec, stream=s, graph=True) as p:
         Q = cq.empty_colmajor(m, n, device="cuda")
         R = cq.empty_colmajor(n, n, device="cuda")
+        counts = []
         for _ in range(3):  # capture, then replay twice
+            l0 = cq.cqr2_launch_count()
             p.factor(A1, Q, R)
+            counts.append(cq.cqr2_launch_count() - l0)
             torch.cuda.synchronize()
             assert bool((Q == Qd).all()) and bool((R == Rd).all())
+        assert counts[0] > 10 and counts[1] == counts[0] == counts[2]  # a replay counts the graph's kernels
         p.factor(A2, Q, R)  # new arguments: a new capture
         torch.cuda.synchronize()
         assert bool((Q == Qd2).all()) and bool((R == Rd2).all())
@@ -277,7 +281,9 @@ def test_batch_graph_replay(cq, prec):
         for p in probs:
             p[0].mul_(2.0)
         torch.cuda.synchronize()
+        l0 = cq.cqr2_launch_count()
         b.factor(probs)  # replay on the new contents
+        assert cq.cqr2_launch_count() - l0 >= 1 + 4 * 10  # the grouped launch and the planned problems' kernels
         for i, p in enumerate(probs):
             assert np.array_equal(to_host(p[1]), ref[i][0]), i
             assert np.array_equal(to_host(p[2]), 2.0 * ref[i][1]), i
