@@ -668,9 +668,14 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
             // B slices lie back to back in shared memory (one 1024-byte pitch
             // per 8 rows throughout) and group g = s + t is the BN-column
             // accumulator at column BN g, so each product lands in its group.
+            // The S - s products of slice s go in as few MMAs as N <= 256
+            // allows, split evenly: an MMA below N = 192 costs a fixed ~75
+            // clocks, so 3 + 3 beats 4 + 2 and 3 + 2 beats 4 + 1.
+            constexpr int NMMA_MAX = (S + C::TMAX - 1) / C::TMAX;
 #pragma unroll
-            for (int t0 = 0; t0 < S - s; t0 += C::TMAX) {
-              const int nt = S - s - t0 < C::TMAX ? S - s - t0 : C::TMAX;
+            for (int q = 0, t0 = 0; q < NMMA_MAX && t0 < S - s; ++q) {
+              const int nm = (S - s + C::TMAX - 1) / C::TMAX;  // MMAs for this slice
+              const int nt = (S - s - t0 + (nm - q) - 1) / (nm - q);
               if (s == 0 && wait_acc) {  // first write of groups t0 .. t0+nt-1 in this buffer
 #pragma unroll
                 for (int g = t0; g < t0 + nt; ++g)
@@ -684,6 +689,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
               mma_bf16(d, da, db, idesc_n, (s == 0 && first) ? 0u : 1u);
 #pragma unroll
               for (int k = 1; k < OZ_BK / 16; ++k) mma_bf16(d, da + DA_K16 * k, db + 2 * k, idesc_n, 1u);
+              t0 += nt;
             }
             if (!ok) break;
             mma_commit(&aempty[slot]);
