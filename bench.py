@@ -600,22 +600,27 @@ def bench_ours(args, ws, rank, local):
     plan.close()
     if rank == 0 and not args.quick and args.serving_requests > 0:
         # serving leg: a bounded stream of least-squares requests (Poisson
-        # arrivals at 2000/s, m in [1024, 262144], n in {16..256}, kappa in
-        # [1, 1e5]) under a 64 GB HBM budget: continuous batching over 8
-        # stream slots with small requests grouped into one launch, the same
-        # without grouping, and one request at a time
+        # arrivals, m in [1024, 262144], n in {16..256}, kappa in [1, 1e5])
+        # under a 64 GB HBM budget: continuous batching over 8 stream slots
+        # with small requests grouped into one launch, the same without
+        # grouping, and one request at a time
         del A, Q, R
         torch.cuda.empty_cache()
         from paper_1710_08471_gb300 import serving
 
         pool = serving.InputPool(262144, (16, 32, 64, 128, 256), seed=100)
         sv = {}
-        for name, prec, slots, gmax in (("ozaki_continuous", 1, 8, 64), ("ozaki_continuous_ungrouped", 1, 8, 1),
-                                        ("ozaki_one_at_a_time", 1, 1, 1), ("fp64_continuous", 0, 8, 64),
-                                        ("fp64_one_at_a_time", 0, 1, 1)):
+        # at the offered 2000 requests/s (overload: latency is queueing), and
+        # at rates each precision sustains (latency is service time)
+        nreq = args.serving_requests
+        for name, prec, slots, gmax, rate, count in (
+                ("ozaki_continuous", 1, 8, 64, 2000.0, nreq), ("ozaki_continuous_ungrouped", 1, 8, 1, 2000.0, nreq),
+                ("ozaki_one_at_a_time", 1, 1, 1, 2000.0, nreq), ("fp64_continuous", 0, 8, 64, 2000.0, nreq),
+                ("fp64_one_at_a_time", 0, 1, 1, 2000.0, nreq),
+                ("ozaki_continuous_at_800_per_s", 1, 8, 64, 800.0, nreq),
+                ("fp64_continuous_at_100_per_s", 0, 8, 64, 100.0, max(1, nreq // 2))):
             try:
-                sv[name] = serving.run_workload(args.serving_requests, 2000.0, 100, prec, slots, 64e9, pool=pool,
-                                                group_max=gmax)
+                sv[name] = serving.run_workload(count, rate, 100, prec, slots, 64e9, pool=pool, group_max=gmax)
             except Exception as ex:  # a serving leg must not cost the main line
                 sv[name] = {"error": repr(ex)}
         out["serving"] = sv
