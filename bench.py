@@ -228,7 +228,7 @@ def workload_config(args, ws: int) -> dict:
     m, n, kappa, seed, desc = WORKLOADS[args.workload]
     fused = args.variant == "fused" and args.precision == "fp64"
     return {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
-            "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth,
+            "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth, "graph": args.graph,
             "parallelism": f"replicas{ws}" if ws > 1 else "single",
             "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"}
 
@@ -456,10 +456,11 @@ def bench_ours(args, ws, rank, local):
     Q = cq.empty_colmajor(m, n, device=dev)
     R = cq.empty_colmajor(n, n, device=dev)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
+    # a graph needs a stream of its own (not the legacy default stream)
+    stream = torch.cuda.Stream(device=dev) if args.graph else torch.cuda.current_stream()
 
-    def make_plan(precision, fz, depth=0):
-        pl = cq.Plan(m, n, precision=PRECISIONS[precision], fused=fz, stream=stream)
+    def make_plan(precision, fz, depth=0, graph=False):
+        pl = cq.Plan(m, n, precision=PRECISIONS[precision], fused=fz, stream=stream, graph=graph)
         if depth:
             pl.set_inverse_depth(depth)
         return pl
@@ -512,10 +513,16 @@ def bench_ours(args, ws, rank, local):
         return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
 
-    plan = make_plan(args.precision, fused, args.inverse_depth)
+    plan = make_plan(args.precision, fused, args.inverse_depth, graph=args.graph)
     clocks = ClockSampler(local)
     clocks.start()
-    ms_local, launches, per_stage = timed(plan, args.steps, args.warmup, True)
+    if args.graph:
+        # stage timers run eagerly (they bypass the graph); the step time is
+        # the graph replay's
+        _, _, per_stage = timed(plan, max(2, args.steps // 2), 1, True)
+        ms_local, launches, _ = timed(plan, args.steps, args.warmup, False)
+    else:
+        ms_local, launches, per_stage = timed(plan, args.steps, args.warmup, True)
     clk = clocks.stop()
     flops = nominal_flops(m, n)
     value, ms_step = replica_throughput(ws, flops, ms_local)
@@ -644,6 +651,8 @@ def main():
                     help="rows of the workload the CPU oracle runs on (default: all for the error check, "
                          "2^21 for --impl reference)")
     ap.add_argument("--quick", action="store_true", help="device timing only (no e2e / oracle legs)")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay the factorization from a captured CUDA graph (CQR2_GRAPH); for launch-bound sizes")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests in the serving leg (0 = skip)")
     args = ap.parse_args()

@@ -44,7 +44,7 @@ def test_reference_and_gpu_arms_share_the_config():
     spec.loader.exec_module(bench)
 
     class A:
-        workload, variant, precision, inverse_depth = "wide512", "fused", "ozaki", 0
+        workload, variant, precision, inverse_depth, graph = "wide512", "fused", "ozaki", 0, False
 
     cfg = bench.workload_config(A, 1)
     assert cfg["m"] == 1 << 21 and cfg["n"] == 512 and cfg["variant"] == "plain"  # fusion is FP64-only
