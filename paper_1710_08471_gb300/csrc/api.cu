@@ -261,7 +261,8 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
   {
     Stage st(p, CQR2_STAGE_TRMM);
     TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
-                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws,
+                 cholinv_splitk_doubles()));
   }
   return CQR2_OK;
 }
@@ -362,7 +363,8 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   {
     Stage st(p, CQR2_STAGE_TRMM);
     TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
-                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws,
+                 cholinv_splitk_doubles()));
   }
   return CQR2_OK;
 }
@@ -417,7 +419,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   if (r != CQR2_OK) return r;
   Stage st(p, CQR2_STAGE_TRMM);
   TRY(gemm_f64(n, n, n, 1.0, p->Rt, n, p->R0, n, 0.0, dR, ldr,
-               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s));
+               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws, cholinv_splitk_doubles()));
   return CQR2_OK;
 }
 
@@ -837,7 +839,8 @@ cqr2_status_t cqr2_trmm_upper(cqr2_plan_t p, const double* dR2, int64_t ld2, con
   if (r != CQR2_OK) return r;
   const int n = (int)p->n;
   TRY(gemm_f64(n, n, n, 1.0, dR2, ld2, dR1, ld1, 0.0, dR, ldr,
-               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, p->stream));
+               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, p->stream, p->skws,
+               cholinv_splitk_doubles()));
   return CQR2_OK;
 }
 

@@ -15,6 +15,7 @@
 // and never traps.
 #include <algorithm>
 
+#include "fp64_rsqrt.cuh"
 #include "kernels.h"
 
 namespace cqr2 {
@@ -101,16 +102,18 @@ __device__ int cholinv_smem(SmallSmem& sm, int n) {
     sm.T[j * BLD + i] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // One division per pivot (its reciprocal); the column and the inverse's
-  // row are then scaled by multiplication: on GB300 an FP64 division costs
-  // many times a multiply, and the n pivots are a serial chain.
+  // One reciprocal square root per pivot (a short Newton sequence); the
+  // column and the inverse's row are then scaled by multiplication: on GB300
+  // an FP64 division or square root costs many times a multiply, and the n
+  // pivots are a serial chain.
   for (int k = 0; k < n; ++k) {
     if (t == 0) {
       const double d = sm.S[k * BLD + k];
       if ((!(d > 0.0) || !isfinite(d)) && sm.fail_pivot < 0) sm.fail_pivot = k;
-      const double l = sqrt(d);
+      double l, rl;
+      chol_rsqrt(d, &rl, &l);
       sm.S[k * BLD + k] = l;
-      sm.rd[k] = 1.0 / l;
+      sm.rd[k] = rl;
     }
     __syncthreads();
     const double rl = sm.rd[k];

@@ -16,6 +16,7 @@
 // with NaNs instead of trapping, so the context stays usable).
 #include <algorithm>
 
+#include "fp64_rsqrt.cuh"
 #include "kernels.h"
 
 namespace cqr2 {
@@ -38,16 +39,18 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   }
   __syncthreads();
   // Right-looking Cholesky. GB300 runs about two FP64 operations per clock per
-  // SM, so each pivot's reciprocal is formed once (thread 0) and the column
-  // is scaled by multiplication; the reciprocals also scale the inverse below.
+  // SM, so each pivot's square root and reciprocal come from one short Newton
+  // sequence (thread 0) and the column is scaled by multiplication; the
+  // reciprocals also scale the inverse below.
   __shared__ double rdiag[NB];
   for (int k = 0; k < nb; ++k) {
     if (t == 0) {
       const double d = S[k * LD + k];
       if (!(d > 0.0) || !isfinite(d)) report_pivot(st, pass, off + k, d);
-      const double l = sqrt(d);
+      double l, rl;
+      chol_rsqrt(d, &rl, &l);  // few FP64 operations: the pivots are a serial chain
       S[k * LD + k] = l;
-      rdiag[k] = 1.0 / l;
+      rdiag[k] = rl;
     }
     __syncthreads();
     const double rl = rdiag[k];
