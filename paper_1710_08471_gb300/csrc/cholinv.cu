@@ -11,7 +11,7 @@
 // result is the same factorization, rounded in a different order.
 //
 // The base case holds the block in shared memory, runs a right-looking
-// Cholesky and then a right-looking triangular inverse, and reports the first
+// Cholesky with the right-looking triangular inverse interleaved, and reports the first
 // non-positive or non-finite pivot in the device status word (it keeps going
 // with NaNs instead of trapping, so the context stays usable).
 #include <algorithm>
@@ -31,42 +31,59 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   extern __shared__ double smem[];
   double* S = smem;            // S(i, j) = S[j * LD + i], lower part
   double* T = smem + NB * LD;  // right-looking inverse workspace / result
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int t = threadIdx.x;
   for (int e = t; e < nb * nb; e += 256) {
     const int i = e % nb, j = e / nb;
     S[j * LD + i] = (i >= j) ? Wk[i + (int64_t)j * ldk] : 0.0;
     T[j * LD + i] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // Right-looking Cholesky. GB300 runs about two FP64 operations per clock per
-  // SM, so each pivot's square root and reciprocal come from one short Newton
-  // sequence (thread 0) and the column is scaled by multiplication; the
-  // reciprocals also scale the inverse below.
+  // Right-looking Cholesky with the right-looking inverse interleaved, and a
+  // look-ahead of one pivot. GB300 issues an FP64 warp instruction at a small
+  // fraction of the FP32 rate, and the pivots are a serial chain, so step k
+  // runs in two phases:
+  //   1. column k of L and row k of Y = L^-1 are scaled by 1/l_kk;
+  //   2. warp 0 applies step k to column k+1 and then forms pivot k+1 (its
+  //      square root and reciprocal from a short Newton sequence), while the
+  //      other warps apply step k to the rest of the trailing matrix and to
+  //      the rows of Y below k.
+  // Every element sees the same operations in the same order as the plain
+  // factorization followed by the plain inverse.
   __shared__ double rdiag[NB];
+  auto pivot = [&](int k) {
+    const double d = S[k * LD + k];
+    if (!(d > 0.0) || !isfinite(d)) report_pivot(st, pass, off + k, d);
+    double l, rl;
+    chol_rsqrt(d, &rl, &l);
+    S[k * LD + k] = l;
+    rdiag[k] = rl;
+  };
+  const int warp = t >> 5, lane = t & 31;
+  if (t == 0) pivot(0);
+  __syncthreads();
+  const int u = t - 32, ux = u & 15, uy = u >> 4;  // warps 1..7: a 16 x 14 grid
   for (int k = 0; k < nb; ++k) {
-    if (t == 0) {
-      const double d = S[k * LD + k];
-      if (!(d > 0.0) || !isfinite(d)) report_pivot(st, pass, off + k, d);
-      double l, rl;
-      chol_rsqrt(d, &rl, &l);  // few FP64 operations: the pivots are a serial chain
-      S[k * LD + k] = l;
-      rdiag[k] = rl;
+    const double rl = rdiag[k];
+    if (warp == 0) {
+      for (int i = k + 1 + lane; i < nb; i += 32) S[k * LD + i] *= rl;
+    } else if (warp == 1) {
+      for (int j = lane; j <= k; j += 32) T[j * LD + k] *= rl;
     }
     __syncthreads();
-    const double rl = rdiag[k];
-    for (int i = k + 1 + t; i < nb; i += 256) S[k * LD + i] *= rl;
-    __syncthreads();
-    for (int j = k + 1 + tx; j < nb; j += 16)
-      for (int i = j + ty; i < nb; i += 16) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
-    __syncthreads();
-  }
-  // Right-looking inverse: solve L Y = I one row of Y at a time.
-  for (int k = 0; k < nb; ++k) {
-    const double rkk = rdiag[k];
-    for (int j = t; j <= k; j += 256) T[j * LD + k] *= rkk;
-    __syncthreads();
-    for (int j = tx; j <= k; j += 16)
-      for (int i = k + 1 + ty; i < nb; i += 16) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+    if (warp == 0) {
+      if (k + 1 < nb) {
+        const double lk1 = S[k * LD + k + 1];
+        for (int i = k + 1 + lane; i < nb; i += 32)
+          S[(k + 1) * LD + i] = fma(-S[k * LD + i], lk1, S[(k + 1) * LD + i]);
+        __syncwarp();
+        if (lane == 0) pivot(k + 1);
+      }
+    } else {
+      for (int j = k + 2 + ux; j < nb; j += 16)
+        for (int i = j + uy; i < nb; i += 14) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
+      for (int j = ux; j <= k; j += 16)
+        for (int i = k + 1 + uy; i < nb; i += 14) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+    }
     __syncthreads();
   }
   for (int e = t; e < nb * nb; e += 256) {
