@@ -64,11 +64,11 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@e784700eafced348": 2942021000,
-    "k_ozaki_gemm<7,QFORM>@tall@e784700eafced348": 23536168000,
-    "k_ozaki_gemm<7,GRAM>@mid@e784700eafced348": 1893238000,
-    "k_ozaki_gemm<7,GRAM>@tall@e784700eafced348": 15145904000,
-    "k_cqr2_small_batched@batch@8c8b0dcb96907e0e": 5301001000,
+    "k_ozaki_gemm<7,QFORM>@mid@d631c4be522ef64f": 2939573760,
+    "k_ozaki_gemm<7,QFORM>@tall@d631c4be522ef64f": 23516590080,
+    "k_ozaki_gemm<7,GRAM>@mid@d631c4be522ef64f": 1893062400,
+    "k_ozaki_gemm<7,GRAM>@tall@d631c4be522ef64f": 15144499200,
+    "k_cqr2_small_batched@batch@c56aa36f0d944e5a": 5306968320,
 }
 
 
