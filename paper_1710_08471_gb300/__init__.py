@@ -258,6 +258,15 @@ def cqr2_autotune(m: int, n: int, precision: int = CQR2_FP64) -> dict:
     return {"gram_ctas": res.gram_ctas, "fused": bool(res.fused), "ms": res.ms, "candidates": res.candidates}
 
 
+def cqr2_autotune_batch(n: int, count: int) -> int:
+    """Time a batch of `count` problems of width n through the grouped kernel
+    and through plans for doubling m, and set the routing limit on m n^2 used
+    by batches created later; returns it."""
+    lim = C.c_int64()
+    N.check(N.load().cqr2_autotune_batch(int(n), int(count), C.byref(lim)), "cqr2_autotune_batch")
+    return lim.value
+
+
 def cqr2_tune_set_small_limit(limit: int) -> None:
     N.check(N.load().cqr2_tune_set_small_limit(int(limit)), "cqr2_tune_set_small_limit")
 

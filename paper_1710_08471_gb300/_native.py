@@ -73,6 +73,7 @@ SIGNATURES = {
     "cqr2_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(BatchConfig), _P]),
     "cqr2_batch_factor": (C.c_int, [_P, C.POINTER(Problem), C.c_int32, C.POINTER(Info)]),
     "cqr2_batch_info": (C.c_int, [_P, C.c_int32, C.POINTER(Info)]),
+    "cqr2_autotune_batch": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]),
     "cqr2_batch_destroy": (None, [_P]),
     "cqr2_autotune": (C.c_int, [_I64, _I64, C.c_int32, C.POINTER(TuneResult)]),
     "cqr2_tune_set_small_limit": (C.c_int, [_I64]),

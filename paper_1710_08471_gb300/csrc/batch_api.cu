@@ -368,14 +368,25 @@ cqr2_status_t cqr2_autotune(int64_t m, int64_t n, int32_t precision, cqr2_tune_r
     return CQR2_ERR_OOM;
   }
   cudaStream_t s;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return CQR2_ERR_CUDA;
-  // A well-conditioned scratch matrix: columns of the identity pattern plus a
-  // smooth fill (the timings do not depend on the values).
-  if (cudaMemsetAsync(A, 0, mn, s) != cudaSuccess) return CQR2_ERR_CUDA;
-  for (int64_t j = 0; j < n; ++j) {
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(A);
+    cudaFree(Q);
+    cudaFree(R);
+    return CQR2_ERR_CUDA;
+  }
+  // A well-conditioned scratch matrix: the first n rows are the identity
+  // (the timings do not depend on the values).
+  bool filled = cudaMemsetAsync(A, 0, mn, s) == cudaSuccess;
+  for (int64_t j = 0; filled && j < n; ++j) {
     const double one = 1.0;
-    if (cudaMemcpyAsync(A + j + j * m, &one, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return CQR2_ERR_CUDA;
+    filled = cudaMemcpyAsync(A + j + j * m, &one, sizeof(double), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  }
+  if (!filled) {
+    cudaStreamDestroy(s);
+    cudaFree(A);
+    cudaFree(Q);
+    cudaFree(R);
+    return CQR2_ERR_CUDA;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -430,6 +441,93 @@ cqr2_status_t cqr2_autotune(int64_t m, int64_t n, int32_t precision, cqr2_tune_r
   out->fused = bestE.fused;
   out->ms = bestE.ms;
   out->candidates = tried;
+  return CQR2_OK;
+}
+
+cqr2_status_t cqr2_autotune_batch(int64_t n, int32_t count, int64_t* limit_out) {
+  if (n < 1 || n > BATCH_SMALL_MAX_N || count < 1 || !limit_out) return CQR2_ERR_INVALID_ARG;
+  *limit_out = 0;
+  // Largest m measured: keep the scratch (one A shared by all problems, a Q
+  // and an R each) near 1 GB.
+  int64_t m_cap = std::max<int64_t>(n, ((int64_t)1 << 30) / ((int64_t)count * n * 8 * 2));
+  m_cap = std::min<int64_t>(m_cap, (int64_t)1 << 20);
+  double *A = nullptr, *Q = nullptr, *R = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cqr2_batch_t grouped = nullptr, planned = nullptr;
+  auto cleanup = [&]() {
+    if (s) cudaStreamSynchronize(s);
+    cqr2_batch_destroy(grouped);
+    cqr2_batch_destroy(planned);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(A);
+    cudaFree(Q);
+    cudaFree(R);
+    cudaGetLastError();
+  };
+  if (cudaMalloc(&A, (size_t)m_cap * n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Q, (size_t)count * m_cap * n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&R, (size_t)count * n * n * sizeof(double)) != cudaSuccess) {
+    cleanup();
+    return CQR2_ERR_OOM;
+  }
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemsetAsync(A, 0, (size_t)m_cap * n * sizeof(double), s) != cudaSuccess) {
+    cleanup();
+    return CQR2_ERR_CUDA;
+  }
+  for (int64_t j = 0; j < n; ++j) {  // identity on top: well conditioned for every m
+    const double one = 1.0;
+    if (cudaMemcpyAsync(A + j + j * m_cap, &one, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cleanup();
+      return CQR2_ERR_CUDA;
+    }
+  }
+  // the same problems routed to the grouped kernel, and to plans
+  cqr2_batch_config_t cg{(int64_t)1 << 62, 4, 1, 0}, cp{0, 4, 1, 0};
+  if (cqr2_batch_create(&grouped, count, CQR2_FP64, &cg, s) != CQR2_OK ||
+      cqr2_batch_create(&planned, count, CQR2_FP64, &cp, s) != CQR2_OK) {
+    cleanup();
+    return CQR2_ERR_OOM;
+  }
+  std::vector<cqr2_problem_t> probs(count);
+  auto time_batch = [&](cqr2_batch_t b, int64_t m, float* ms) -> cqr2_status_t {
+    for (int i = 0; i < count; ++i)
+      probs[i] = cqr2_problem_t{m, n, A, m_cap, Q + (size_t)i * m_cap * n, m_cap, R + (size_t)i * n * n, n,
+                                nullptr, nullptr};
+    cqr2_status_t r = cqr2_batch_factor(b, probs.data(), count, nullptr);  // warm (plans, first loads)
+    if (r != CQR2_OK) return r;
+    if (cudaEventRecord(e0, s) != cudaSuccess) return CQR2_ERR_CUDA;
+    const int reps = 3;
+    for (int k = 0; k < reps; ++k)
+      if ((r = cqr2_batch_factor(b, probs.data(), count, nullptr)) != CQR2_OK) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return CQR2_ERR_CUDA;
+    if (cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return CQR2_ERR_CUDA;
+    *ms /= reps;
+    return CQR2_OK;
+  };
+  // double m from n while the grouped launch is at least as fast
+  int64_t limit = 0;
+  for (int64_t m = std::max<int64_t>(n, 64); m <= m_cap; m *= 2) {
+    float tg = 0.f, tp = 0.f;
+    cqr2_status_t r = time_batch(grouped, m, &tg);
+    if (r == CQR2_OK) r = time_batch(planned, m, &tp);
+    if (r != CQR2_OK) {
+      cleanup();
+      return r;
+    }
+    if (tg > tp) break;
+    limit = m * n * n;
+  }
+  cleanup();
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_small_limit = limit;
+  }
+  *limit_out = limit;
   return CQR2_OK;
 }
 

@@ -311,3 +311,22 @@ def test_autotune_records_table(cq):
         A = synth.make_matrix(50000, 128, 1e4, seed=3)
         Q, R, _ = p.factor(to_dev(A))
     check(A, to_host(Q), to_host(R), 1e4)
+
+
+def test_autotune_batch_routing_limit(cq):
+    """The batch routing autotuner measures the grouped kernel against plans
+    and sets the limit later batches use (restored afterwards)."""
+    try:
+        lim = cq.cqr2_autotune_batch(32, 152)
+        assert lim >= 0 and lim % (32 * 32) == 0
+        assert f"small_work_limit={lim}" in cq.cqr2_tune_table()
+        # a batch created now routes by the tuned limit, and still factors correctly
+        shapes = [(max(64, lim // (32 * 32)), 32, 1e3), (64, 32, 10.0), (4 * max(64, lim // (32 * 32)) + 1, 32, 1e2)]
+        mats, probs = _problems(cq, shapes, seed0=900)
+        with cq.Batch(len(probs)) as b:
+            infos = b.factor(probs)
+        for A, (_, Q, R), inf, (m, n, kappa) in zip(mats, probs, infos, shapes):
+            assert inf.status == 0
+            check(A, to_host(Q), to_host(R), kappa)
+    finally:
+        cq.cqr2_tune_set_small_limit(32768 * 64 * 64)
