@@ -296,8 +296,9 @@ cqr2_status_t cqr2_autotune(int64_t m, int64_t n, int32_t precision, cqr2_tune_r
 /* Tune the batch routing limit for batches of `count` problems of width n
  * (1 <= n <= 64): times the same batch through the grouped kernel and
  * through plans on 4 streams for m = max(n, 64), doubling while the grouped
- * launch is at least as fast (up to about 1 GB of scratch), and sets the
- * limit on m n^2 used by batches created later (cfg NULL) to the largest m n^2
+ * launch is at least as fast (up to about 4 GB of scratch, so the result is a
+ * lower bound when the grouped launch still wins there), and sets the limit
+ * on m n^2 used by batches created later (cfg NULL) to the largest m n^2
  * where it was; 0 if it never was. *limit_out receives it. Synchronizes;
  * allocates. */
 cqr2_status_t cqr2_autotune_batch(int64_t n, int32_t count, int64_t* limit_out);

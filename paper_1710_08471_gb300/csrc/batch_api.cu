@@ -448,8 +448,8 @@ cqr2_status_t cqr2_autotune_batch(int64_t n, int32_t count, int64_t* limit_out) 
   if (n < 1 || n > BATCH_SMALL_MAX_N || count < 1 || !limit_out) return CQR2_ERR_INVALID_ARG;
   *limit_out = 0;
   // Largest m measured: keep the scratch (one A shared by all problems, a Q
-  // and an R each) near 1 GB.
-  int64_t m_cap = std::max<int64_t>(n, ((int64_t)1 << 30) / ((int64_t)count * n * 8 * 2));
+  // and an R each) near 4 GB.
+  int64_t m_cap = std::max<int64_t>(n, ((int64_t)1 << 32) / ((int64_t)count * n * 8 * 2));
   m_cap = std::min<int64_t>(m_cap, (int64_t)1 << 20);
   double *A = nullptr, *Q = nullptr, *R = nullptr;
   cudaStream_t s = nullptr;
