@@ -513,6 +513,28 @@ def bench_ours(args, ws, rank, local):
         return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
 
+    def step_roofline(precision, fz, ms_step, clk):
+        """The whole step against its roofline: max(compulsory bytes / HBM,
+        work / the pipes' peaks) over the measured time. Compulsory bytes:
+        the 4 trips of an m x n FP64 matrix (32mn: A in and Q out, twice).
+        Work: nominal FP64 flops at the FP64 peak, or, for split precision,
+        the kept slice products at the sustained BF16 peak plus CholInv and
+        R2 R1 (FP64) at the FP64 peak."""
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        fp64 = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6
+        t_bw = 32.0 * m * n / (peaks["hbm_gbs"] * 1e9) * 1e3
+        if SLICES[precision] == 0:
+            t_fl = nominal_flops(m, n) / fp64 * 1e3
+            pipe = "fp64"
+        else:
+            tensor = sum(stage_work(m, n, precision, fz).values())
+            t_fl = (tensor / (peaks["bf16_sustained"] * 1e12) + (4 * n ** 3 / 3 + n ** 3 / 3) / fp64) * 1e3
+            pipe = "bf16 tensor + fp64"
+        rt = max(t_bw, t_fl)
+        return {"t_hbm_ms": t_bw, "t_compute_ms": t_fl, "compute_pipe": pipe,
+                "bound": "hbm" if t_bw >= t_fl else "compute", "roofline_ms": rt, "frac": rt / ms_step,
+                "peaks": peaks["src"]}
+
     plan = make_plan(args.precision, fused, args.inverse_depth, graph=args.graph)
     clocks = ClockSampler(local)
     clocks.start()
@@ -537,6 +559,7 @@ def bench_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "roofline": roofline_of(per_stage, args.precision, fused, clk),
         "vs_fp64_peak": {"achieved": value / ws, "peak": fp64_peak, "frac": value / ws / fp64_peak},
+        "step_roofline": step_roofline(args.precision, fused, ms_local, clk),
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "clocks": clk,
     }
@@ -579,7 +602,8 @@ def bench_ours(args, ws, rank, local):
                 variants[name] = {"ms_per_step": ms_v, "tflops": flops / (ms_v * 1e-3) / 1e12,
                                   "speedup_vs_main": ms_step / ms_v,
                                   "stages_ms": {k: round(v, 4) for k, v in st_v.items()},
-                                  "roofline": roofline_of(st_v, prec, fz, clk), "errors": errors()}
+                                  "roofline": roofline_of(st_v, prec, fz, clk),
+                                  "step_roofline": step_roofline(prec, fz, ms_v, clk), "errors": errors()}
                 pl.close()
             except Exception as ex:  # a variant must not cost the main line
                 variants[name] = {"error": repr(ex)}
