@@ -231,12 +231,19 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
   cudaStream_t s = p->stream;
   if (!pass_base) TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   TRY(hx_wait_input(p, s));
+  // Up to OZAKI_FUSED_COLMAX_MAX_N columns the pass-1 Q-form also folds Q1's
+  // column maxima into oz_colmax, so pass 2 skips the column-max sweep.
+  const bool fused_cmax = n <= OZAKI_FUSED_COLMAX_MAX_N;
   for (int pass = 1; pass <= 2; ++pass) {
     const double* X = pass == 1 ? dA : dQ;
     const int64_t ldx = pass == 1 ? lda : ldq;
     {
       Stage st(p, CQR2_STAGE_SPLIT);
-      TRY(ozaki_colmax(X, ldx, m, n, p->oz_colmax, p->oz_cexp, s));
+      if (pass == 2 && fused_cmax) {
+        TRY(ozaki_exps(p->oz_colmax, n, p->oz_cexp, s));
+      } else {
+        TRY(ozaki_colmax(X, ldx, m, n, p->oz_colmax, p->oz_cexp, s));
+      }
       TRY(ozaki_slice_cols(X, ldx, m, n, S, p->oz_cexp, p->oz_planes, s));
     }
     {
@@ -255,7 +262,9 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     {
       // The Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
       Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
-      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_fexp, dQ, ldq, p->st, s));
+      const bool cm = pass == 1 && fused_cmax;
+      if (cm) TRY(cudaMemsetAsync(p->oz_colmax, 0, (size_t)n * sizeof(unsigned long long), s));
+      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_fexp, dQ, ldq, p->st, s, cm ? p->oz_colmax : nullptr));
     }
   }
   {

@@ -143,8 +143,13 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
 // polls) and records a timeout in *st, as the split-precision GEMM does.
 cudaError_t ozaki_selftest_wait(long long polls, DevStatus* st, cudaStream_t s);
 // Q = X R^-1 from X's column slices (the Gram's planes) and R^-1's slices.
+// With colmax (zeroed by the caller) and n <= OZAKI_FUSED_COLMAX_MAX_N, the
+// column maxima of Q are folded into it as k_colmax would compute them.
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
-                        DevStatus* st, cudaStream_t s);
+                        DevStatus* st, cudaStream_t s, unsigned long long* colmax = nullptr);
+constexpr int OZAKI_FUSED_COLMAX_MAX_N = 1024;
+// Column exponents from column maxima (the second half of ozaki_colmax).
+cudaError_t ozaki_exps(const unsigned long long* colmax, int n, int* cexp, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched
 // One problem of a grouped launch (same layout as cqr2_problem_t).

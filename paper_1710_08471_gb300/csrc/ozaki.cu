@@ -350,7 +350,20 @@ struct OzParams {
   double* out;             // Gram: partial[split][n][n]; Q-form: Q
   int64_t ldo;
   DevStatus* st;
+  // Q-form, n <= OZ_CMAX_N: if set, the column maxima of |Q| (as the FP64
+  // bit pattern of a value with the maximum's exponent, k_colmax's meaning)
+  // are atomically folded in, so the next pass needs no column-max sweep
+  unsigned long long* cmax;
 };
+constexpr int OZ_CMAX_N = OZAKI_FUSED_COLMAX_MAX_N;
+
+// Order-preserving 32-bit key of |x| for the column exponent: the high word
+// of its bit pattern (sign cleared), and back to a bit pattern with that
+// high word. exp_from_bits of the result equals that of the column's maximum
+// except for a column whose maximum lies below 2^-1042 (a high word of zero),
+// which reads as all zero instead of subnormal.
+__device__ __forceinline__ uint32_t oz_exp_key(double x) { return (uint32_t)__double2hiint(x) & 0x7FFFFFFFu; }
+__device__ __forceinline__ unsigned long long oz_key_bits(uint32_t k) { return (unsigned long long)k << 32; }
 
 // One work item: an output tile and its contraction range.
 struct OzItem {
@@ -527,6 +540,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
   uint64_t* accempty = accfull + NBUF * S;
   uint64_t* drainbar = accempty + NBUF * S;  // MMA completion on the timeout path
   uint32_t* tmem_slot = (uint32_t*)(drainbar + 1);
+  uint32_t* s_key = tmem_slot + 4;  // Q-form with p.cmax: column max keys [n]
+  const bool fuse_cmax = MODE == OZ_QFORM && p.cmax != nullptr;
+  if (fuse_cmax)
+    for (int c = threadIdx.x; c < p.n; c += blockDim.x) s_key[c] = 0u;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -768,6 +785,9 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
 #undef OZ_DRAIN
       }
       if (!ok) break;
+      uint32_t ck[NEB];  // Q-form: column max keys of this thread's row
+#pragma unroll
+      for (int cc = 0; cc < NEB; ++cc) ck[cc] = 0u;
       if (row < nrow) {
         const int ea2 = MODE == OZ_GRAM ? p.eA[row] : ea;
         double* out = MODE == OZ_GRAM ? p.out + (int64_t)w.split * p.n * p.n : p.out;
@@ -779,11 +799,23 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
             const int e2 = MODE == OZ_QFORM ? eb[cc < NEB ? cc : 0] : p.eB[col];
             // Gram: exact rounding; Q-form: within one ulp (far below its
             // truncation error), with a shorter integer sequence
-            out[row + col * ld] = (ea2 >= EXP_NONFINITE || e2 >= EXP_NONFINITE)
-                                      ? __longlong_as_double(0x7FF8000000000000ll)
-                                  : MODE == OZ_GRAM ? oz_xy_to_double(X[cc], Y[cc], ea2 + e2 - 14 - 48)
-                                                    : oz_xy_to_double_fast(X[cc], Y[cc], ea2 + e2 - 14 - 48);
+            const double v = (ea2 >= EXP_NONFINITE || e2 >= EXP_NONFINITE)
+                                 ? __longlong_as_double(0x7FF8000000000000ll)
+                             : MODE == OZ_GRAM ? oz_xy_to_double(X[cc], Y[cc], ea2 + e2 - 14 - 48)
+                                               : oz_xy_to_double_fast(X[cc], Y[cc], ea2 + e2 - 14 - 48);
+            out[row + col * ld] = v;
+            if (MODE == OZ_QFORM) ck[cc < NEB ? cc : 0] = oz_exp_key(v);
           }
+        }
+      }
+      if (fuse_cmax) {
+        // the warp's 32 rows reduced per column, then one shared atomic
+        const unsigned mask = __activemask();
+#pragma unroll
+        for (int cc = 0; cc < NEB; ++cc) {
+          const uint32_t mk = __reduce_max_sync(mask, ck[cc]);
+          const int64_t col = w.j0 + cs * CPT + cc;
+          if (lane == __ffs(mask) - 1 && col < p.n && mk != 0u) atomicMax(&s_key[col], mk);
         }
       }
     }
@@ -791,6 +823,9 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  if (fuse_cmax)
+    for (int c = threadIdx.x; c < p.n; c += blockDim.x)
+      if (s_key[c] != 0u) atomicMax(p.cmax + c, oz_key_bits(s_key[c]));
   if (warp == 0) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -852,11 +887,13 @@ EncodeTiledFn encode_fn() {
 template <int S, int MODE, int BN, int EPI, int NGRP>
 cudaError_t launch_oz(const CUtensorMap& a, const CUtensorMap& b, const OzParams& p, dim3 grid, cudaStream_t s) {
   using Cfg = OzCfg<S, BN, EPI, NGRP>;
-  static_assert(Cfg::SMEM <= 227 * 1024, "shared memory per CTA");
+  // the Q-form also holds the column max keys (after the TMEM slot)
+  constexpr size_t SMEM = Cfg::SMEM + (MODE == OZ_QFORM ? 4 * OZ_CMAX_N + 16 : 0);
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
   auto kern = k_ozaki_gemm<S, MODE, BN, EPI, NGRP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, b, p);
+  kern<<<grid, Cfg::THREADS, SMEM, s>>>(a, b, p);
   count_launch();
   return cudaGetLastError();
 }
@@ -945,6 +982,12 @@ cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes,
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t ozaki_exps(const unsigned long long* colmax, int n, int* cexp, cudaStream_t s) {
+  k_exps_from_max<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(colmax, n, cexp);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned long long* colmax, int* cexp,
                          cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)n * sizeof(unsigned long long), s);
@@ -1008,9 +1051,10 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
 }
 
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
-                        DevStatus* st, cudaStream_t s) {
+                        DevStatus* st, cudaStream_t s, unsigned long long* colmax) {
   const OzGeom g = ozaki_geometry(m, n);
   OzParams p{};
+  p.cmax = n <= OZ_CMAX_N ? colmax : nullptr;
   p.m = m;
   p.n = n;
   p.eA = nullptr;  // X enters through its column slices, whose exponents are folded into R^-1
