@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
                              : MODE == OZ_GRAM ? oz_xy_to_double(X[cc], Y[cc], ea2 + e2 - 14 - 48)
                                                : oz_xy_to_double_fast(X[cc], Y[cc], ea2 + e2 - 14 - 48);
             out[row + col * ld] = v;
-            if (MODE == OZ_QFORM) ck[cc < NEB ? cc : 0] = oz_exp_key(v);
+            if (MODE == OZ_QFORM && fuse_cmax) ck[cc < NEB ? cc : 0] = oz_exp_key(v);
           }
         }
       }
