@@ -64,10 +64,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@d631c4be522ef64f": 2939573760,
-    "k_ozaki_gemm<7,QFORM>@tall@d631c4be522ef64f": 23516590080,
-    "k_ozaki_gemm<7,GRAM>@mid@d631c4be522ef64f": 1893062400,
-    "k_ozaki_gemm<7,GRAM>@tall@d631c4be522ef64f": 15144499200,
+    "k_ozaki_gemm<7,QFORM>@mid@438bba48f733e7ec": 2938563328,
+    "k_ozaki_gemm<7,QFORM>@tall@438bba48f733e7ec": 23508506624,
+    "k_ozaki_gemm<7,GRAM>@mid@438bba48f733e7ec": 1892568064,
+    "k_ozaki_gemm<7,GRAM>@tall@438bba48f733e7ec": 15140544512,
     "k_cqr2_small_batched@batch@c56aa36f0d944e5a": 5306968320,
 }
 
