@@ -363,6 +363,9 @@ def main(argv=None) -> None:
     ap.add_argument("--group-work-limit", type=int, default=1 << 24, help="grouped when n <= 64 and m n^2 <= this")
     args = ap.parse_args(argv)
     pool = InputPool(262144, (16, 32, 64, 128, 256), seed=args.seed)
+    # warm-up (not reported): first device allocations and kernel loads
+    run_workload(min(300, args.requests), args.rate, args.seed + 1, args.precision, args.slots, args.budget_gb * 1e9,
+                 pool=pool)
     out = {"continuous": run_workload(args.requests, args.rate, args.seed, args.precision, args.slots,
                                       args.budget_gb * 1e9, pool=pool, group_max=args.group_max,
                                       group_work_limit=args.group_work_limit),
