@@ -94,3 +94,25 @@ def test_header_constants_match_binding():
                  "CQR2_OZAKI_BF16_S6", "CQR2_OK", "CQR2_ERR_INVALID_ARG", "CQR2_ERR_NOT_SPD", "CQR2_ERR_OOM",
                  "CQR2_ERR_TIMEOUT", "CQR2_ERR_UNSUPPORTED"):
         assert getattr(_native, name) == vals[name], name
+
+
+def test_header_is_plain_c():
+    """include/cqr2.h compiles as C99 (no C++ in the ABI), and a C program
+    that calls every group of entry points links against the library."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = (
+        '#include "cqr2.h"\n'
+        "int main(void) {\n"
+        "  cqr2_problem_t p = {0}; cqr2_info_t i = {0}; cqr2_batch_config_t c = {0}; cqr2_tune_result_t t = {0};\n"
+        "  (void)p; (void)i; (void)c; (void)t;\n"
+        "  return cqr2_status_string(CQR2_OK)[0] == 'C' ? 0 : 1;\n"
+        "}\n"
+    )
+    out = subprocess.run([cc, "-x", "c", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", HEADER_DIR, "-"],
+                         input=src, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
