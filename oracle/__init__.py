@@ -14,7 +14,6 @@ from .cholqr2 import (  # noqa: F401
     lstsq,
     nominal_flops,
     orthogonality,
-    q_rows,
     rel_error,
     residual,
     right_solve,

@@ -283,15 +283,6 @@ def lstsq(A: np.ndarray, b: np.ndarray, keep: bool = False):
     return x
 
 
-def q_rows(A_rows: np.ndarray, Rinv1: np.ndarray, Rinv2: np.ndarray) -> np.ndarray:
-    """Rows of CQR2's Q for selected rows of A: (A_rows R1^-1) R2^-1.
-
-    Q = A R^-1 acts on each row of A independently (Algorithm CQR step 3), so
-    these are exactly the corresponding rows of the full oracle's Q.
-    """
-    return (np.asarray(A_rows, dtype=np.float64) @ Rinv1) @ Rinv2
-
-
 # ---------------------------------------------------------------- error norms
 
 def orthogonality(Q: np.ndarray) -> float:

@@ -402,3 +402,153 @@ def test_right_solve_planted_missing_update_is_caught():
     B = np.random.default_rng(1).standard_normal((30, 20))
     X = mod.right_solve(B, L, Y, 2)
     assert np.linalg.norm(X @ L.T - B) > 1e-3 * np.linalg.norm(B)
+
+
+# ------------------------------------- the error norms every parity test uses
+#
+# orthogonality, residual and rel_error are the yardsticks of the GPU parity
+# tests and of the bench's error report, so they are pinned to values fixed by
+# exact arithmetic: dyadic inputs whose products and sums are exact in FP64,
+# with the expected norms worked out in rational arithmetic (fractions), not by
+# the functions under test.
+
+from fractions import Fraction  # noqa: E402
+
+
+def _hadamard(k: int) -> np.ndarray:
+    """Sylvester Hadamard matrix of order 2^k (entries +-1, H^T H = 2^k I)."""
+    H = np.ones((1, 1))
+    for _ in range(k):
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def _frob_exact(E) -> Fraction:
+    """Squared Frobenius norm of a matrix of Fractions."""
+    return sum((x * x for row in E for x in row), Fraction(0))
+
+
+def _ortho_case():
+    """Q = U M with U = H_16 / 4 (exactly orthonormal columns) and a dyadic
+    upper-triangular M: Q^T Q - I = M^T M - I exactly."""
+    U = _hadamard(4)[:, [1, 6, 11]] / 4.0
+    Mf = [[Fraction(1), Fraction(1, 4), Fraction(0)],
+          [Fraction(0), Fraction(1), Fraction(1, 2)],
+          [Fraction(0), Fraction(0), Fraction(3, 4)]]
+    M = np.array([[float(x) for x in r] for r in Mf])
+    n = 3
+    E = [[sum((Mf[k][i] * Mf[k][j] for k in range(n)), Fraction(0)) - (1 if i == j else 0) for j in range(n)]
+         for i in range(n)]
+    return U @ M, _frob_exact(E)
+
+
+def test_orthogonality_exact_value():
+    Q, e2 = _ortho_case()
+    assert e2 == Fraction(170, 256)  # worked by hand: diag (0, 1/16, -3/16), off-diagonal 1/4, 1/2
+    assert oracle.orthogonality(Q) == pytest.approx(math.sqrt(170) / 16, rel=4 * EPS)
+
+
+def test_orthogonality_of_exactly_orthonormal_columns_is_zero():
+    # columns with disjoint supports far apart (+-1/2 on four rows each)
+    m = 3 * (1 << 18) + 5
+    Q = np.zeros((m, 4))
+    rows = [[0, 1 << 18, (1 << 19) + 3, m - 1], [5, 77, 1 << 17, m - 2], [9, 10, 11, 12], [m - 3, m - 4, 200, 300]]
+    for j, rs in enumerate(rows):
+        Q[rs, j] = [0.5, -0.5, 0.5, 0.5]
+    assert oracle.orthogonality(Q) == 0.0
+    Q[(1 << 19) + 3, 0] *= 2.0  # one entry doubled: column norm^2 1 + 3/4, nothing else changes
+    assert oracle.orthogonality(Q) == pytest.approx(0.75, rel=2 * EPS)
+
+
+def _residual_case(block_offsets):
+    """A = Q R + E over several 2^18-row blocks and a ragged tail, with Q, R,
+    E dyadic so that Q R is exact; returns (A, Q, R, exact residual^2)."""
+    m, n = 3 * (1 << 18) + 5, 2
+    i = np.arange(m)
+    Q4 = np.stack([(i % 3) - 1, (i % 5) - 2], axis=1)  # 4 Q as integers
+    Q = Q4 / 4.0
+    R = np.array([[2.0, 1.0], [0.0, 4.0]])
+    QR4 = Q4 @ R.astype(np.int64)  # 4 Q R, exact integers
+    E4 = np.zeros((m, n), dtype=np.int64)  # 4 E
+    for (r, c, v) in block_offsets:
+        E4[r, c] = v
+    A4 = QR4 + E4
+    A = A4 / 4.0
+    num = int(np.sum(E4 * E4))
+    den = int(np.sum(A4 * A4))  # int64: no rounding
+    return A, Q, R, Fraction(num, den)
+
+
+# one entry of E in each 2^18-row block, past the middle of the block, and one
+# in the ragged last rows
+_E_ENTRIES = [(200_000, 0, 12), ((1 << 18) + 150_001, 1, -16), ((1 << 19) + 140_000, 0, 48),
+              (3 * (1 << 18) + 4, 1, 4)]
+
+
+def test_residual_exact_value_across_blocks():
+    A, Q, R, r2 = _residual_case(_E_ENTRIES)
+    want = math.sqrt(r2.numerator) / math.sqrt(r2.denominator)
+    assert oracle.residual(A, Q, R) == pytest.approx(want, rel=8 * EPS)
+    # the blocking is an implementation detail: any block size gives the same value
+    assert oracle.residual(A, Q, R, block=1000) == pytest.approx(want, rel=8 * EPS)
+    # and Q R = A gives exactly zero
+    assert oracle.residual(Q @ R, Q, R) == 0.0
+
+
+def test_rel_error_exact_values():
+    X = synth.make_matrix(50, 7, 1e2, seed=61)
+    assert oracle.rel_error(2.0 * X, X) == pytest.approx(1.0, rel=2 * EPS)
+    assert oracle.rel_error(X, X) == 0.0
+    # ||D||_F / ||Xr||_F with D and Xr dyadic: sqrt(9 + 16) / sqrt(4 + 1 + 4 + 16)
+    Xr = np.array([[2.0, 0.0], [1.0, -2.0], [0.0, 4.0]])
+    D = np.array([[0.0, 3.0], [0.0, 0.0], [-4.0, 0.0]])
+    assert oracle.rel_error(Xr + D, Xr) == pytest.approx(1.0, rel=2 * EPS)
+    assert oracle.rel_error(Xr + D / 5.0, Xr) == pytest.approx(0.2, rel=4 * EPS)
+
+
+_YARDSTICK_MUTATIONS = {
+    "ortho_no_identity": ("    G[np.diag_indices_from(G)] -= 1.0\n", ""),
+    "ortho_outer_product": ("    G = Q.T @ Q\n", "    G = Q @ Q.T\n"),
+    "ortho_two_norm": ("    return float(np.linalg.norm(G))", "    return float(np.linalg.norm(G, 2))"),
+    "residual_unsquared": ("        num += float(np.sum(d * d))", "        num += float(np.sum(np.abs(d)))"),
+    "residual_no_root_denominator": ("    return math.sqrt(num) / math.sqrt(den)", "    return math.sqrt(num) / den"),
+    "residual_last_block_dropped": ("    for r0 in range(0, A.shape[0], block):",
+                                    "    for r0 in range(0, A.shape[0] - block, block):"),
+    "residual_half_blocks": ("        a = A[r0:r0 + block]\n        d = Q[r0:r0 + block] @ R - a",
+                             "        a = A[r0:r0 + block // 2]\n        d = Q[r0:r0 + block // 2] @ R - a"),
+    "rel_error_wrong_normaliser": ("np.linalg.norm(X - X_ref) / np.linalg.norm(X_ref)",
+                                   "np.linalg.norm(X - X_ref) / np.linalg.norm(X)"),
+}
+
+
+def _yardstick_mutant(key: str) -> types.ModuleType:
+    src = inspect.getsource(ocq)
+    old, new = _YARDSTICK_MUTATIONS[key]
+    assert src.count(old) == 1, key
+    mod = types.ModuleType(f"oracle_mutant_{key}")
+    exec(compile(src.replace(old, new), f"<mutant {key}>", "exec"), mod.__dict__)
+    return mod
+
+
+def _yardstick_pins_pass(mod) -> bool:
+    try:
+        Q, e2 = _ortho_case()
+        if mod.orthogonality(Q) != pytest.approx(math.sqrt(170) / 16, rel=4 * EPS):
+            return False
+        A, Qr, R, r2 = _residual_case(_E_ENTRIES)
+        if mod.residual(A, Qr, R) != pytest.approx(math.sqrt(r2.numerator) / math.sqrt(r2.denominator),
+                                                     rel=8 * EPS):
+            return False
+        X = synth.make_matrix(50, 7, 1e2, seed=61)
+        return mod.rel_error(2.0 * X, X) == pytest.approx(1.0, rel=2 * EPS)
+    except Exception:
+        return False
+
+
+def test_yardstick_pins_accept_oracle():
+    assert _yardstick_pins_pass(ocq)
+
+
+@pytest.mark.parametrize("key", sorted(_YARDSTICK_MUTATIONS))
+def test_yardstick_pins_reject_planted_mistake(key):
+    assert not _yardstick_pins_pass(_yardstick_mutant(key))
