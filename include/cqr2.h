@@ -325,17 +325,24 @@ int64_t cqr2_tune_table(char* buf, int64_t size);
  * the middle of a job. This entry point needs no plan and calls no
  * cudaMalloc, cudaFree or allocating library routine: its split-m partial
  * Gram tiles live in one file-scope device array of
- * CQR2_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds
- * until the process exits.
+ * CQR2_NOALLOC_SCRATCH_BYTES. A device takes that array when the library's
+ * Gram module is first loaded on it (the first Gram kernel of any entry point,
+ * or the first cqr2_syrk_noalloc call, there) and holds it until the process
+ * exits.
  *   dA: m x n (lda >= m) device input; dW: n x n (ldw >= n) device output,
- *   both triangles written. stream: cudaStream_t as void* (NULL = default).
- *   Errors: CQR2_ERR_INVALID_ARG for null pointers, n < 1, m < n or a bad
- *   leading dimension; CQR2_ERR_UNSUPPORTED for n > CQR2_NOALLOC_MAX_N (the
- *   partial tiles of one row range would not fit the scratch); CQR2_ERR_CUDA
- *   if a CUDA call fails. Larger m only means fewer row ranges.
- * The first call on a device looks up the scratch array's device address
- * (with that device current) and caches it; make that first call before any
- * stream capture. All calls share the one array and it keeps the last call's
+ *   both triangles written. Both must be device (or managed) memory of the
+ *   current device. stream: cudaStream_t as void* (NULL = default).
+ *   Errors: CQR2_ERR_INVALID_ARG for null pointers, n < 1, m < n, a bad
+ *   leading dimension, or a pointer that is host memory or belongs to another
+ *   device; CQR2_ERR_UNSUPPORTED for n > CQR2_NOALLOC_MAX_N (the partial
+ *   tiles of one row range would not fit the scratch); CQR2_ERR_CUDA if a
+ *   CUDA call fails. Larger m only means fewer row ranges.
+ * The first call in a CUDA context looks up the scratch array's device
+ * address there (cudaGetSymbolAddress, with that context current) and caches
+ * it under the context's unique id, so a new context (another device, a
+ * driver-API context, or the primary context again after cudaDeviceReset)
+ * gets its own lookup; make that first call before any stream capture. All
+ * calls on a device share the one array and it keeps the last call's
  * contents; every entry a call reads is written earlier in the same call, so
  * nothing needs clearing, but calls whose work overlaps on the GPU (other
  * streams, other host threads) race on the array: serialize them. */

@@ -27,8 +27,10 @@ constexpr int KC = 32;  // rows per staged chunk
 
 // Scratch of the allocation-free Gram entry point (cqr2_syrk_noalloc): the
 // split-m partial tiles live in this fixed device array instead of a plan's
-// workspace. Every GPU that loads this library holds it until the process
-// exits.
+// workspace. It belongs to this file's module: a device holds it from the
+// first time the module is loaded there (the first Gram kernel or
+// cqr2_syrk_noalloc call on that device, under CUDA's default lazy loading)
+// until the process exits.
 constexpr size_t NOALLOC_DOUBLES = CQR2_NOALLOC_SCRATCH_BYTES / sizeof(double);
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
@@ -248,27 +250,86 @@ cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double*
 
 namespace {
 
-// Device address of g_noalloc_scratch, looked up once per device (with that
-// device current) on the first call there. Host code must not use the
-// symbol itself: on the host it names a stand-in, not device memory.
-constexpr int MAX_DEVICES = 64;
+// Device address of g_noalloc_scratch, looked up once per CUDA context (with
+// that context current) on the first call there, and cached. Host code must
+// not use the symbol itself: on the host it names a stand-in, not device
+// memory. The cache is keyed by the context's process-unique id
+// (cuCtxGetId), so a context made current by the driver API, or the new
+// primary context after a cudaDeviceReset, gets its own lookup instead of a
+// stale address; where the driver lacks cuCtxGetId the key is the device
+// ordinal (primary contexts only, no cudaDeviceReset in between).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+constexpr int MAX_CONTEXTS = 64;
 std::mutex g_scratch_mu;
-double* g_scratch_addr[MAX_DEVICES] = {};
+struct ScratchEntry {
+  unsigned long long key;
+  double* addr;
+};
+ScratchEntry g_scratch[MAX_CONTEXTS];
+int g_scratch_used = 0;
 
-cudaError_t noalloc_scratch(double** out) {
+template <typename F>
+F driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPoint(name, &p, cudaEnableDefault, &q) != cudaSuccess || q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(p);
+}
+
+// Key of the current context: its unique id with the top bit set, or the
+// device ordinal when the driver cannot tell contexts apart (or no context is
+// current yet; the entry point's pointer checks have made the runtime's
+// context current by then).
+cudaError_t context_key(unsigned long long* key) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, cqr2::g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+  static CtxGetCurrentFn get_cur = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) {
+    *key = id | (1ull << 63);
+    return cudaSuccess;
   }
-  *out = g_scratch_addr[dev];
+  *key = (unsigned long long)dev;
   return cudaSuccess;
+}
+
+cudaError_t noalloc_scratch(double** out) {
+  unsigned long long key = 0;
+  cudaError_t e = context_key(&key);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  for (int i = 0; i < g_scratch_used; ++i)
+    if (g_scratch[i].key == key) {
+      *out = g_scratch[i].addr;
+      return cudaSuccess;
+    }
+  if (g_scratch_used == MAX_CONTEXTS) return cudaErrorInvalidDevice;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, cqr2::g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  g_scratch[g_scratch_used++] = {key, static_cast<double*>(p)};
+  *out = static_cast<double*>(p);
+  return cudaSuccess;
+}
+
+// A pointer the kernels may dereference on the current device: device or
+// managed memory of this device. Host and unregistered pointers, and memory
+// of another device, are rejected (cudaPointerGetAttributes allocates
+// nothing).
+bool on_current_device(const void* ptr) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();  // clear the error the failed query recorded
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -278,6 +339,7 @@ extern "C" cqr2_status_t cqr2_syrk_noalloc(const double* dA, int64_t m, int64_t 
   using namespace cqr2;
   if (!dA || !dW || n < 1 || m < n || lda < m || ldw < n) return CQR2_ERR_INVALID_ARG;
   if (n > CQR2_NOALLOC_MAX_N) return CQR2_ERR_UNSUPPORTED;
+  if (!on_current_device(dA) || !on_current_device(dW)) return CQR2_ERR_INVALID_ARG;
   const GramGeom g0 = gram_geometry(m, (int)n, 0);
   const int64_t per_split = (int64_t)g0.ntiles_total * g0.T * g0.T;
   const int64_t max_splits = (int64_t)NOALLOC_DOUBLES / per_split;

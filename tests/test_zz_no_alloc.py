@@ -5,9 +5,10 @@ its own pool allocator, or code where a cudaMalloc could fail or stall in the
 middle of a job). For them cqr2_syrk_noalloc computes W = A^T A with its
 partial sums in a fixed scratch array inside the library. This file checks,
 through the C ABI, that two calls in a row give the same Gram as the plan-based
-entry point cqr2_syrk, within the Gram tolerance the other tests use
-(|W - W_ref| <= 2 m eps (|A|^T |A|) elementwise). The file is named so that
-pytest collects it last.
+entry point cqr2_syrk and as the CPU oracle's Syrk, within the Gram tolerance
+the other tests use (|W - W_ref| <= 2 m eps (|A|^T |A|) elementwise), and
+that pointers the kernels could not read on this device are refused before
+anything is launched. The file is named so that pytest collects it last.
 """
 from __future__ import annotations
 
@@ -16,6 +17,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from gpu_util import EPS, to_dev, to_host
 
@@ -54,17 +56,22 @@ def test_noalloc_matches_plan_syrk_twice(cq, m, n, kappa):
     A = synth.make_matrix(m, n, kappa, seed=m + 7 * n)
     Ad = to_dev(A)
     with cq.Plan(m, n) as p:
-        W_ref = to_host(p.syrk(Ad))
+        W_plan = to_host(p.syrk(Ad))
+    W_oracle = oracle.syrk(A)
     absA = np.abs(A)
     bound = 2 * m * EPS * (absA.T @ absA)
     outs = []
-    for _ in range(2):
+    for call in range(2):
         W = cq.empty_colmajor(n, n, device="cuda")
         W.fill_(float("nan"))
-        assert _noalloc_raw(cq, m, n, Ad, W) == cq.CQR2_OK
+        if call == 0:
+            assert _noalloc_raw(cq, m, n, Ad, W) == cq.CQR2_OK
+        else:  # the public Python wrapper over the same entry point
+            cq.cqr2_syrk_noalloc(m, n, Ad, W, stream=torch.cuda.current_stream())
         torch.cuda.synchronize()
         Wh = to_host(W)
-        assert np.all(np.abs(Wh - W_ref) <= bound + 1e-300)
+        assert np.all(np.abs(Wh - W_plan) <= bound + 1e-300)
+        assert np.all(np.abs(Wh - W_oracle) <= bound + 1e-300)
         assert np.array_equal(Wh, Wh.T)
         outs.append(Wh)
     assert np.array_equal(outs[0], outs[1])
@@ -94,3 +101,29 @@ def test_noalloc_rejects_sizes_beyond_maximum(cq):
     assert lib.cqr2_syrk_noalloc(p, n, n, n, p, n, None) == cq.CQR2_ERR_UNSUPPORTED
     assert lib.cqr2_syrk_noalloc(p, 10, 20, 10, p, 20, None) == cq.CQR2_ERR_INVALID_ARG
     assert lib.cqr2_syrk_noalloc(None, 10, 5, 10, p, 5, None) == cq.CQR2_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_host_pointers(cq):
+    """A host array (pageable or pinned) is refused with INVALID_ARG before any
+    kernel is launched."""
+    import torch
+
+    from paper_1710_08471_gb300 import _native
+
+    lib = _native.load()
+    m, n = 256, 8
+    hA = np.asfortranarray(synth.make_matrix(m, n, None, seed=3))
+    W = cq.empty_colmajor(n, n, device="cuda")
+    Wp = ctypes.c_void_p(W.data_ptr())
+    assert lib.cqr2_syrk_noalloc(ctypes.c_void_p(hA.ctypes.data), m, n, m, Wp, n, None) == cq.CQR2_ERR_INVALID_ARG
+    pinned = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+    assert lib.cqr2_syrk_noalloc(ctypes.c_void_p(pinned.data_ptr()), m, n, m, Wp, n, None) == cq.CQR2_ERR_INVALID_ARG
+    Ad = to_dev(hA)
+    hW = np.zeros((n, n), order="F")
+    assert lib.cqr2_syrk_noalloc(ctypes.c_void_p(Ad.data_ptr()), m, n, m, ctypes.c_void_p(hW.ctypes.data), n,
+                                 None) == cq.CQR2_ERR_INVALID_ARG
+    # and the device pair still works afterwards
+    assert lib.cqr2_syrk_noalloc(ctypes.c_void_p(Ad.data_ptr()), m, n, m, Wp, n, None) == cq.CQR2_OK
+    torch.cuda.synchronize()
+    absA = np.abs(hA)
+    assert np.all(np.abs(to_host(W) - oracle.syrk(hA)) <= 2 * m * EPS * (absA.T @ absA) + 1e-300)
