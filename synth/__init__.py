@@ -7,6 +7,9 @@ that the oracle and the GPU library can be fed the very same bits.
 from .matrices import (  # noqa: F401
     ROW_BLOCK,
     gaussian,
+    graded_rows,
+    scaled_column,
+    spiked_column,
     log_sigma,
     random_orthogonal,
     make_matrix,

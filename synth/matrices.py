@@ -131,3 +131,38 @@ def request_stream(count: int, seed: int, rate: float, m_lo: int = 1024, m_hi: i
     ks = np.exp(g.uniform(np.log(kappa_lo), np.log(kappa_hi), size=count))
     return [dict(id=i, t=float(t[i]), m=int(ms[i]), n=int(ns[i]), kappa=float(ks[i]), seed=seed + i)
             for i in range(count)]
+
+
+# ------------------------------------------------ inputs that stress scaling
+
+def graded_rows(m: int, n: int, kappa: float, seed: int, span: float = 1e6, mid: int = 0) -> np.ndarray:
+    """m x n matrix with condition number kappa whose row norms spread over
+    about span^2 (12 orders of magnitude for span = 1e6): A = U diag(sigma) V
+    with U the orthonormal factor (LAPACK Householder QR via numpy) of D G,
+    D = diag(10^u), u uniform in [-log10 span, log10 span] per row, G Gaussian.
+    U's rows scale like D, while A keeps the singular values sigma."""
+    g = _gen(seed, mid, 0)
+    G = g.standard_normal((m, n))
+    d = 10.0 ** g.uniform(-np.log10(span), np.log10(span), size=m)
+    U, _ = np.linalg.qr(d[:, None] * G)
+    A = U @ (log_sigma(n, kappa)[:, None] * random_orthogonal(n, seed, mid))
+    return np.asfortranarray(A)
+
+
+def spiked_column(m: int, n: int, kappa: float | None, seed: int, col: int, ratio: float = 1e8,
+                  mid: int = 0) -> np.ndarray:
+    """make_matrix(m, n, kappa, seed) with one entry of column `col` (at a
+    seeded row) set to `ratio` times the column's median magnitude."""
+    A = make_matrix(m, n, kappa, seed, mid)
+    row = int(_gen(seed, mid, 1).integers(0, m))
+    A[row, col] = ratio * float(np.median(np.abs(A[:, col])))
+    return A
+
+
+def scaled_column(m: int, n: int, kappa: float | None, seed: int, col: int, scale: float = 1e-20,
+                  mid: int = 0) -> np.ndarray:
+    """make_matrix(m, n, kappa, seed) with column `col` multiplied by `scale`
+    (a column of all-tiny entries next to O(1) ones)."""
+    A = make_matrix(m, n, kappa, seed, mid)
+    A[:, col] *= scale
+    return A
