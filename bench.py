@@ -301,6 +301,13 @@ def bench_reference_batch(args, ws):
 
 
 def bench_batch(args, ws, rank, local):
+    """The batch workload as the bench line."""
+    out = measure_batch(args.steps, args.warmup, ws, rank, local, args.quick)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def measure_batch(steps: int, warmup: int, ws: int, rank: int, local: int, quick: bool) -> dict:
     """One step = one cqr2_batch_factor call over BATCH_COUNT problems, all
     routed to the persistent grouped kernel, replayed from a captured graph."""
     import torch
@@ -324,7 +331,7 @@ def bench_batch(args, ws, rank, local):
     infos = batch.factor(desc_arr)
     if any(i.status != 0 for i in infos):
         raise SystemExit("batch factorization failed")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.factor(desc_arr, sync=False)
     batch.info()
     torch.cuda.synchronize()
@@ -334,34 +341,34 @@ def bench_batch(args, ws, rank, local):
     l0 = cq.cqr2_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch.factor(desc_arr, sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = cq.cqr2_launch_count() - l0
     barrier(ws)
-    ms_local = e0.elapsed_time(e1) / args.steps
+    ms_local = e0.elapsed_time(e1) / steps
     flops = count * nominal_flops(m, n)
     value, ms_step = replica_throughput(ws, flops, ms_local)
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    fp64_peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
+    fp64_pk = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
     achieved = flops / (ms_local * 1e-3) / 1e12
     out = {
         "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": batch_config(args, ws),
+        "config": batch_config(None, ws),
         "gpu_launches": launches,
         "qr_per_s": ws * count / (ms_step * 1e-3),
         "roofline": {"bound": "alu", "kernel": "k_cqr2_small_batched", "stage": "batch", "achieved": achieved,
-                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "peak": fp64_pk, "unit": "TFLOP/s", "frac": achieved / fp64_pk,
                      "traffic": NCU_TRAFFIC.get(f"k_cqr2_small_batched@batch@{src_sha('batched.cu')}"),
                      "peak_note": f"derived FP64 DFMA peak: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 "
                                   f"flops x {sm_max:.0f} MHz; work = nominal flops of every problem"},
         "clocks": clk,
     }
-    if rank == 0 and not args.quick:
+    if rank == 0 and not quick:
         import oracle
 
         # errors on a sample of problems against the oracle, and the CPU baseline
@@ -387,7 +394,7 @@ def bench_batch(args, ws, rank, local):
         hQ_t = torch.empty((n, count * m), dtype=torch.float64, pin_memory=True)
         hR_t = torch.empty((count * n, n), dtype=torch.float64, pin_memory=True)
         times = []
-        for _ in range(max(2, args.steps // 2)):
+        for _ in range(max(2, steps // 2)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
@@ -403,8 +410,7 @@ def bench_batch(args, ws, rank, local):
                       "h2d_bytes_per_step": count * m * n * 8, "d2h_bytes_per_step": count * (m * n + n * n) * 8,
                       "api": "cqr2_batch_factor with pinned host copies on the batch stream"}
     batch.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 PRECISIONS = {"fp64": 0, "ozaki": 1, "ozaki6": 2}
@@ -439,6 +445,254 @@ def stage_work(m: int, n: int, precision: str, fused: bool) -> dict:
     return {"gram1": gram, "gram2": gram, "qform1": qform, "qform2": qform}
 
 
+def fp64_peak(clk: dict) -> float:
+    """Derived FP64 peak in TFLOP/s at the sampled maximum SM clock."""
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    return FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
+
+
+def roofline_of(per_stage: dict, m: int, n: int, precision: str, fz: bool, clk: dict, workload: str,
+                peaks: dict) -> dict:
+    """Roofline of the dominant stage: its algorithmic work per launch over
+    its CUDA-event time, against the FP64 peak (native) or the sustained BF16
+    tensor peak (split precision)."""
+    work = stage_work(m, n, precision, fz)
+    cands = {k: v for k, v in per_stage.items() if k in work and work[k] > 0}
+    dom = max(cands, key=cands.get)
+    achieved = work[dom] / (per_stage[dom] * 1e-3) / 1e12
+    if SLICES[precision] == 0:
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        peak = fp64_peak(clk)
+        if n <= 256:
+            kern = {"qform1": "k_qform_gram_small" if fz else "k_qform_small", "gram1": "k_gram_tile",
+                    "gram2": "k_gram_tile", "qform2": "k_qform_small"}.get(dom, dom)
+        else:
+            kern = {"qform1": "k_gemm_f64", "qform2": "k_gemm_f64", "gram1": "k_gram_tile",
+                    "gram2": "k_gram_tile"}.get(dom, dom)
+        kfile = {"k_gemm_f64": "gemm.cu", "k_gram_tile": "gram.cu"}.get(kern, "qform.cu")
+        note = f"derived FP64 DFMA peak: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 flops x {sm_max:.0f} MHz"
+        bound = "alu"
+    else:
+        peak = peaks["bf16_sustained"]
+        kern = "k_ozaki_gemm<%d,%s>" % (SLICES[precision], "GRAM" if dom.startswith("gram") else "QFORM")
+        kfile = "ozaki.cu"
+        note = f"{peaks['src']} sustained bf16 tensor peak; work = BF16 flops of the kept slice products"
+        bound = "tensor"
+    traffic = NCU_TRAFFIC.get(f"{kern}@{workload}@{src_sha(kfile)}")
+    return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
+
+
+def step_roofline(m: int, n: int, precision: str, fz: bool, ms_step: float, clk: dict, peaks: dict) -> dict:
+    """The whole step against its roofline: max(compulsory bytes / HBM,
+    work / the pipes' peaks) over the measured time. Compulsory bytes: the 4
+    trips of an m x n FP64 matrix (32mn: A in and Q out, twice). Work:
+    nominal FP64 flops at the FP64 peak, or, for split precision, the kept
+    slice products at the sustained BF16 peak plus CholInv and R2 R1 (FP64)
+    at the FP64 peak."""
+    fp64 = fp64_peak(clk) * 1e12
+    t_bw = 32.0 * m * n / (peaks["hbm_gbs"] * 1e9) * 1e3
+    if SLICES[precision] == 0:
+        t_fl = nominal_flops(m, n) / fp64 * 1e3
+        pipe = "fp64"
+    else:
+        tensor = sum(stage_work(m, n, precision, fz).values())
+        t_fl = (tensor / (peaks["bf16_sustained"] * 1e12) + (4 * n ** 3 / 3 + n ** 3 / 3) / fp64) * 1e3
+        pipe = "bf16 tensor + fp64"
+    rt = max(t_bw, t_fl)
+    return {"t_hbm_ms": t_bw, "t_compute_ms": t_fl, "compute_pipe": pipe,
+            "bound": "hbm" if t_bw >= t_fl else "compute", "roofline_ms": rt, "frac": rt / ms_step,
+            "peaks": peaks["src"]}
+
+
+def timed_plan(pl, A, Q, R, stream, steps: int, warmup: int, profile: bool, ws: int = 1, flush=None):
+    """CUDA-event time per factorization on the plan's stream (ms), kernel
+    launches in the timed region, and per-stage ms when profiling. With
+    `flush` (a device buffer larger than L2) every step is timed alone with
+    the buffer rewritten between steps, outside the timed events."""
+    import torch
+
+    import paper_1710_08471_gb300 as cq
+
+    info = pl.factor(A, Q, R, sync=True)[2]
+    if info.status != 0:
+        raise SystemExit(f"factorization failed: status {info.status}")
+    for _ in range(max(3, warmup)):
+        pl.factor(A, Q, R, sync=False)
+    torch.cuda.synchronize()
+    barrier(ws)
+    pl.set_profiling(profile)
+    l0 = cq.cqr2_launch_count()
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            pl.factor(A, Q, R, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    else:
+        evs = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.add_(1.0)  # rewrite a buffer larger than L2
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pl.factor(A, Q, R, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    launches = cq.cqr2_launch_count() - l0
+    barrier(ws)
+    st = pl.stage_times() if profile else None
+    pl.set_profiling(False)
+    # per step: a stage that runs several times in one factorization (the
+    # split-precision slicing) is summed over its occurrences
+    return ms, launches, {k: v[0] / steps for k, v in st.items() if v[1] > 0} if st else {}
+
+
+def oracle_seconds_one_core(m: int, n: int, kappa, seed: int, repeats: int = 5) -> float | None:
+    """Median seconds of the CPU oracle's CQR2 on one core (a child process
+    with one BLAS thread), or None if that could not be run."""
+    code = ("import sys, time, statistics; sys.path.insert(0, %r); import synth, oracle; "
+            "A = synth.make_matrix(%d, %d, %r, %d, threads=1); ts = []\n"
+            "for _ in range(%d):\n t0 = time.perf_counter(); oracle.cqr2(A); ts.append(time.perf_counter() - t0)\n"
+            "print(statistics.median(ts))") % (ROOT, m, n, kappa, seed, repeats)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, env=env)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
+
+
+def bench_configs(steps: int, warmup: int, local: int, peaks: dict, clk: dict, serving_pool=None) -> dict:
+    """The other configurations of the benchmark plan, measured in the same
+    run (device-timed with CUDA events, errors against the CPU oracle):
+    - small (4096 x 64, the latency-bound case), replayed from a CUDA graph,
+      L2 rewritten between steps (its 2 MB input fits in L2);
+    - wide512 (2^21 x 512, kappa 1e6), native FP64 and split precision (S = 7)
+      at the same shape;
+    - batch (1024 problems of 4096 x 32 in one grouped launch per step);
+    - the 20,000-request least-squares stream at 2000 requests/s, split
+      precision, continuous batching against one request at a time."""
+    import torch
+
+    import oracle
+    import paper_1710_08471_gb300 as cq
+
+    dev = torch.device("cuda", local)
+    out = {}
+
+    def errs(hA, Q, R, Ro):
+        hQ = np.asfortranarray(Q.cpu().numpy())
+        hR = np.asfortranarray(R.cpu().numpy())
+        e = {"orthogonality": oracle.orthogonality(hQ), "residual": oracle.residual(hA, hQ, hR)}
+        if Ro is not None:
+            e["R_rel_vs_oracle"] = oracle.rel_error(hR, Ro)
+        return e
+
+    # ---- small: 4096 x 64, FP64, fused, graph-replayed
+    try:
+        m, n, kappa, seed, desc = WORKLOADS["small"]
+        hA = synth.make_matrix(m, n, kappa, seed)
+        A = cq.colmajor(torch.from_numpy(np.ascontiguousarray(hA.T)).to(dev).t())
+        Q, R = cq.empty_colmajor(m, n, device=dev), cq.empty_colmajor(n, n, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        flush = torch.zeros(64 << 20, dtype=torch.float64, device=dev)  # 512 MB > L2
+        res = {"workload": desc, "m": m, "n": n, "precision": "fp64", "variant": "fused", "graph": True,
+               "l2": "512 MB buffer rewritten between steps (outside the timed events)"}
+        with cq.Plan(m, n, fused=True, stream=stream, graph=True) as pl:
+            ms, launches, _ = timed_plan(pl, A, Q, R, stream, max(20, steps), warmup, False, flush=flush)
+            with cq.Plan(m, n, fused=True, stream=stream) as pe:
+                ms_eager, _, st = timed_plan(pe, A, Q, R, stream, max(20, steps), warmup, True, flush=flush)
+        del flush
+        t0 = time.perf_counter()
+        Qo, Ro = oracle.cqr2(hA)
+        fl = nominal_flops(m, n)
+        pk = fp64_peak(clk)
+        res.update({"ms_per_step": ms, "tflops": fl / (ms * 1e-3) / 1e12, "gpu_launches_per_step": launches / max(20, steps),
+                    "eager_ms_per_step": ms_eager, "eager_stages_ms": {k: round(v, 4) for k, v in st.items()},
+                    "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                                 "frac": fl / (ms * 1e-3) / 1e12 / pk,
+                                 "note": "nominal flops of the whole step over the derived FP64 peak; the step is "
+                                         "latency-bound (two one-CTA CholInv base cases on its critical path)"},
+                    "errors": dict(errs(hA, Q, R, Ro), oracle_orthogonality=oracle.orthogonality(Qo))})
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            oracle.cqr2(hA)
+            ts.append(time.perf_counter() - t0)
+        t1 = oracle_seconds_one_core(m, n, kappa, seed)
+        res["cpu_baseline"] = {"value": fl / statistics.median(ts) / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+                               "kind": "oracle", "sample": "full workload, median of 5",
+                               "one_core_tflops": fl / t1 / 1e12 if t1 else None}
+        out["small"] = res
+    except Exception as ex:  # a configuration must not cost the main line
+        out["small"] = {"error": repr(ex)}
+    torch.cuda.empty_cache()
+
+    # ---- wide512: 2^21 x 512, kappa 1e6, native FP64 against split precision
+    try:
+        m, n, kappa, seed, desc = WORKLOADS["wide512"]
+        hA = synth.make_matrix(m, n, kappa, seed)
+        A = cq.colmajor(torch.from_numpy(np.ascontiguousarray(hA.T)).to(dev).t())
+        Q, R = cq.empty_colmajor(m, n, device=dev), cq.empty_colmajor(n, n, device=dev)
+        stream = torch.cuda.current_stream()
+        res = {"workload": desc, "m": m, "n": n, "kappa": kappa, "l2": "inputs 8.6 GB > 129 MB L2 (no flush)"}
+        fl = nominal_flops(m, n)
+        runs = {}
+        for name, prec, nsteps in (("fp64", "fp64", 3), ("ozaki7", "ozaki", max(5, steps))):
+            with cq.Plan(m, n, precision=PRECISIONS[prec], stream=stream) as pl:
+                ms, launches, st = timed_plan(pl, A, Q, R, stream, nsteps, warmup, True)
+            runs[name] = {"ms_per_step": ms, "tflops": fl / (ms * 1e-3) / 1e12, "steps": nsteps,
+                          "stages_ms": {k: round(v, 4) for k, v in st.items()},
+                          "roofline": roofline_of(st, m, n, prec, False, clk, "wide512", peaks),
+                          "step_roofline": step_roofline(m, n, prec, False, ms, clk, peaks),
+                          "errors": errs(hA, Q, R, None)}
+        t0 = time.perf_counter()
+        Qo, Ro = oracle.cqr2(hA)
+        dt = time.perf_counter() - t0
+        for name, prec in (("fp64", "fp64"), ("ozaki7", "ozaki")):
+            with cq.Plan(m, n, precision=PRECISIONS[prec], stream=stream) as pl:
+                pl.factor(A, Q, R, sync=True)
+            hR = np.asfortranarray(R.cpu().numpy())
+            runs[name]["errors"]["R_rel_vs_oracle"] = oracle.rel_error(hR, Ro)
+        runs["oracle"] = {"orthogonality": oracle.orthogonality(Qo), "residual": oracle.residual(hA, Qo, Ro)}
+        del Qo
+        res.update(runs)
+        res["split_speedup_vs_fp64"] = runs["fp64"]["ms_per_step"] / runs["ozaki7"]["ms_per_step"]
+        res["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": "full workload, one run", "seconds": dt}
+        out["wide512"] = res
+        del A, Q, R, hA
+    except Exception as ex:
+        out["wide512"] = {"error": repr(ex)}
+    torch.cuda.empty_cache()
+
+    # ---- batch: 1024 problems of 4096 x 32 per grouped launch
+    try:
+        out["batch"] = measure_batch(max(5, steps), warmup, 1, 0, local, False)
+    except Exception as ex:
+        out["batch"] = {"error": repr(ex)}
+    torch.cuda.empty_cache()
+
+    # ---- the full request stream of the serving configuration
+    try:
+        from paper_1710_08471_gb300 import serving
+
+        pool = serving_pool or serving.InputPool(262144, (16, 32, 64, 128, 256), seed=100)
+        sv = {"requests": 20000, "rate_per_s": 2000.0, "precision": "split (S = 7)",
+              "inputs": "per-request kappa served from a 21-value grid 1..1e5 (within x1.33 of the draw)"}
+        sv["continuous"] = serving.run_workload(20000, 2000.0, 100, 1, 8, 64e9, pool=pool, group_max=64)
+        sv["one_at_a_time"] = serving.run_workload(20000, 2000.0, 100, 1, 1, 64e9, pool=pool, group_max=1)
+        out["serving_20000"] = sv
+    except Exception as ex:
+        out["serving_20000"] = {"error": repr(ex)}
+    return out
+
+
 def bench_ours(args, ws, rank, local):
     import torch
 
@@ -466,74 +720,7 @@ def bench_ours(args, ws, rank, local):
         return pl
 
     def timed(pl, steps, warmup, profile):
-        info = pl.factor(A, Q, R, sync=True)[2]
-        if info.status != 0:
-            raise SystemExit(f"factorization failed: status {info.status}")
-        for _ in range(warmup):
-            pl.factor(A, Q, R, sync=False)
-        torch.cuda.synchronize()
-        barrier(ws)
-        pl.set_profiling(profile)
-        l0 = cq.cqr2_launch_count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            pl.factor(A, Q, R, sync=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        launches = cq.cqr2_launch_count() - l0
-        barrier(ws)
-        ms = e0.elapsed_time(e1) / steps
-        st = pl.stage_times() if profile else None
-        pl.set_profiling(False)
-        # per step: a stage that runs several times in one factorization (the
-        # split-precision slicing) is summed over its occurrences
-        return ms, launches, {k: v[0] / steps for k, v in st.items() if v[1] > 0} if st else {}
-
-    def roofline_of(per_stage, precision, fz, clk):
-        work = stage_work(m, n, precision, fz)
-        cands = {k: v for k, v in per_stage.items() if k in work and work[k] > 0}
-        dom = max(cands, key=cands.get)
-        achieved = work[dom] / (per_stage[dom] * 1e-3) / 1e12
-        if SLICES[precision] == 0:
-            sm_max = clk.get("sm_max_mhz") or 2070.0
-            peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6 / 1e12
-            kern = {"qform1": "k_qform_gram_small" if fz else "k_qform_small", "gram1": "k_gram_tile",
-                    "gram2": "k_gram_tile", "qform2": "k_qform_small"}.get(dom, dom)
-            kfile = "qform.cu" if "qform" in kern else "gram.cu"
-            note = f"derived FP64 DFMA peak: {FP64_FMA_PER_CLK_PER_SM} FMA/clk/SM x 152 SMs x 2 flops x {sm_max:.0f} MHz"
-            bound = "alu"
-        else:
-            peak = peaks["bf16_sustained"]
-            kern = "k_ozaki_gemm<%d,%s>" % (SLICES[precision], "GRAM" if dom.startswith("gram") else "QFORM")
-            kfile = "ozaki.cu"
-            note = f"{peaks['src']} sustained bf16 tensor peak; work = BF16 flops of the kept slice products"
-            bound = "tensor"
-        traffic = NCU_TRAFFIC.get(f"{kern}@{args.workload}@{src_sha(kfile)}")
-        return {"bound": bound, "kernel": kern, "stage": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note}
-
-    def step_roofline(precision, fz, ms_step, clk):
-        """The whole step against its roofline: max(compulsory bytes / HBM,
-        work / the pipes' peaks) over the measured time. Compulsory bytes:
-        the 4 trips of an m x n FP64 matrix (32mn: A in and Q out, twice).
-        Work: nominal FP64 flops at the FP64 peak, or, for split precision,
-        the kept slice products at the sustained BF16 peak plus CholInv and
-        R2 R1 (FP64) at the FP64 peak."""
-        sm_max = clk.get("sm_max_mhz") or 2070.0
-        fp64 = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * sm_max * 1e6
-        t_bw = 32.0 * m * n / (peaks["hbm_gbs"] * 1e9) * 1e3
-        if SLICES[precision] == 0:
-            t_fl = nominal_flops(m, n) / fp64 * 1e3
-            pipe = "fp64"
-        else:
-            tensor = sum(stage_work(m, n, precision, fz).values())
-            t_fl = (tensor / (peaks["bf16_sustained"] * 1e12) + (4 * n ** 3 / 3 + n ** 3 / 3) / fp64) * 1e3
-            pipe = "bf16 tensor + fp64"
-        rt = max(t_bw, t_fl)
-        return {"t_hbm_ms": t_bw, "t_compute_ms": t_fl, "compute_pipe": pipe,
-                "bound": "hbm" if t_bw >= t_fl else "compute", "roofline_ms": rt, "frac": rt / ms_step,
-                "peaks": peaks["src"]}
+        return timed_plan(pl, A, Q, R, stream, steps, warmup, profile, ws)
 
     plan = make_plan(args.precision, fused, args.inverse_depth, graph=args.graph)
     clocks = ClockSampler(local)
@@ -548,7 +735,7 @@ def bench_ours(args, ws, rank, local):
     clk = clocks.stop()
     flops = nominal_flops(m, n)
     value, ms_step = replica_throughput(ws, flops, ms_local)
-    fp64_peak = FP64_FMA_PER_CLK_PER_SM * 2 * GB300_SMS * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    fp64_pk = fp64_peak(clk)
 
     out = {
         "metric": "CQR2 TFLOP/s (nominal 4mn^2+5n^3/3)", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
@@ -557,9 +744,9 @@ def bench_ours(args, ws, rank, local):
         "data": "synthetic",
         "config": workload_config(args, ws),
         "gpu_launches": launches,
-        "roofline": roofline_of(per_stage, args.precision, fused, clk),
-        "vs_fp64_peak": {"achieved": value / ws, "peak": fp64_peak, "frac": value / ws / fp64_peak},
-        "step_roofline": step_roofline(args.precision, fused, ms_local, clk),
+        "roofline": roofline_of(per_stage, m, n, args.precision, fused, clk, args.workload, peaks),
+        "vs_fp64_peak": {"achieved": value / ws, "peak": fp64_pk, "frac": value / ws / fp64_pk},
+        "step_roofline": step_roofline(m, n, args.precision, fused, ms_local, clk, peaks),
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "clocks": clk,
     }
@@ -605,6 +792,10 @@ def bench_ours(args, ws, rank, local):
                       "d2h_gbs": (m * n * 8 + n * n * 8) / (d2h_ms * 1e-3) / 1e9 if d2h_ms else None,
                       "api": "cqr2_factor_host (pinned host buffers)",
                       "plain_copy_probe": {"before": probe_before, "after": copy_rate()}}
+        # the same probe at the top level of the line as well: the pinned
+        # host<->device copy rate of this machine bounds the end-to-end figure
+        out["copy_probe"] = dict(out["e2e"]["plain_copy_probe"], bytes=m * n * 8,
+                                 note="one cudaMemcpyAsync of pinned A to the device and back, GB/s")
         # CPU FP64 oracle of the same workload: errors and the CPU baseline
         rows, dt, Qo, Ro = run_oracle_sample(hA, args.oracle_rows or m)
         sample = (f"full workload ({desc})" if rows == m else f"first {rows} of {m} rows of the workload ({desc})")
@@ -639,13 +830,15 @@ def bench_ours(args, ws, rank, local):
                 variants[name] = {"ms_per_step": ms_v, "tflops": flops / (ms_v * 1e-3) / 1e12,
                                   "speedup_vs_main": ms_step / ms_v,
                                   "stages_ms": {k: round(v, 4) for k, v in st_v.items()},
-                                  "roofline": roofline_of(st_v, prec, fz, clk),
-                                  "step_roofline": step_roofline(prec, fz, ms_v, clk), "errors": errors()}
+                                  "roofline": roofline_of(st_v, m, n, prec, fz, clk, args.workload, peaks),
+                                  "step_roofline": step_roofline(m, n, prec, fz, ms_v, clk, peaks),
+                                  "errors": errors()}
                 pl.close()
             except Exception as ex:  # a variant must not cost the main line
                 variants[name] = {"error": repr(ex)}
         out["variants"] = variants
     plan.close()
+    pool = None
     if rank == 0 and not args.quick and args.serving_requests > 0:
         # serving leg: a bounded stream of least-squares requests (Poisson
         # arrivals, m in [1024, 262144], n in {16..256}, kappa in [1, 1e5])
@@ -676,6 +869,12 @@ def bench_ours(args, ws, rank, local):
             except Exception as ex:  # a serving leg must not cost the main line
                 sv[name] = {"error": repr(ex)}
         out["serving"] = sv
+    if rank == 0 and not args.quick and args.configs:
+        # the plan's other configurations, each with its own timing and errors
+        if "A" in locals():
+            del A, Q, R
+        torch.cuda.empty_cache()
+        out["configs"] = bench_configs(args.steps, args.warmup, local, peaks, clk, serving_pool=pool)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -700,6 +899,8 @@ def main():
                     help="replay the factorization from a captured CUDA graph (CQR2_GRAPH); for launch-bound sizes")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests in the serving leg (0 = skip)")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the other configurations (small, wide512, batch, the 20,000-request stream)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -374,20 +374,30 @@ def main(argv=None) -> None:
     print(json.dumps(out))
 
 
+def kappa_grid(lo: float = 1.0, hi: float = 1e5, per_decade: int = 4) -> list[float]:
+    """Condition numbers log-spaced from lo to hi, per_decade per decade."""
+    k = max(1, round(per_decade * math.log10(hi / lo)))
+    return [lo * (hi / lo) ** (i / k) for i in range(k + 1)]
+
+
 class InputPool:
     """Device-resident synthetic inputs for request streams: for every n and
-    a few condition-number buckets, one m_max x n matrix built by the seeded
-    generator (synth.make_matrix) on the host and copied to the device once; a
-    request of m rows uses the first m rows. The request's kappa is rounded to
-    the nearest bucket (log scale)."""
+    every condition number of a log-spaced grid (by default 1 .. 1e5 at four
+    per decade, 21 values), one m_max x n matrix A = G diag(sigma) V built by
+    the seeded generator (synth.make_matrix) on the host and copied to the
+    device once; a request of m rows uses the first m rows. A request's kappa,
+    drawn log-uniform per request, is served by the nearest grid value, within
+    a factor 10^(1/8) ~ 1.33 at the default grid (the inputs cannot be formed
+    per request without putting an m x n x n product of the generator on the
+    GPU next to the work being timed)."""
 
-    def __init__(self, m_max: int, n_values, kappas=(1e1, 1e3, 1e5), seed: int = 100):
+    def __init__(self, m_max: int, n_values, kappas=None, seed: int = 100):
         import numpy as np
         import torch
 
         import synth
 
-        self.kappas = list(kappas)
+        self.kappas = list(kappas) if kappas is not None else kappa_grid()
         self.A = {}
         for n in n_values:
             for i, k in enumerate(self.kappas):
@@ -399,6 +409,10 @@ class InputPool:
     def bucket(self, kappa: float) -> int:
         lk = math.log10(max(kappa, 1.0))
         return min(range(len(self.kappas)), key=lambda i: abs(math.log10(self.kappas[i]) - lk))
+
+    def kappa_of(self, kappa: float) -> float:
+        """The grid condition number a request drawn with `kappa` is served with."""
+        return self.kappas[self.bucket(kappa)]
 
     def request(self, rid: int, t: float, m: int, n: int, kappa: float) -> Request:
         i = self.bucket(kappa)
