@@ -60,8 +60,22 @@ typedef enum {
  *   BF16 tensor cores from 7 error-free slices of every FP64 entry (about 55
  *   significant bits, Ozaki scheme) with exact accumulation; CholInv and
  *   R = R2 R1 stay native FP64. Not part of the paper. n <= 16384.
+ *   Admissible inputs: every entry is cut with its column's shared exponent
+ *   (the power of two 2^e above the column's largest entry), so the accuracy
+ *   is normwise and degrades with a column's crest ratio c_j =
+ *   sqrt(m) 2^e_j / ||a_j||_2 (about 5 to 10 for Gaussian-like columns).
+ *   Tested within ten times the FP64 bounds for kappa(A) <= 1e7 and c_j up to
+ *   about 150 (rows whose norms span twelve orders of magnitude, a column
+ *   entry 1e8 times its column's median, columns scaled by 1e-20 or 1e15);
+ *   the residual grows about like c_j 2^-55.
  * CQR2_OZAKI_BF16_S6: the same with 6 slices (about 47 bits): faster, with
- *   errors within 10x of the FP64 bounds for kappa(A) <= 1e6. */
+ *   errors within 10x of the FP64 bounds for kappa(A) <= 1e4 when every
+ *   crest ratio is at most 16. The plan checks the crest ratios on the device
+ *   (A's after the first Gram, Q1's before the second) and, where one exceeds
+ *   16, runs the rest of the factorization with 7 slices
+ *   (cqr2_plan_split_slices reports which);
+ *   at larger kappa the 6-slice residual grows (about 1e-12 at kappa 1e6,
+ *   m = 2^23). */
 typedef enum { CQR2_FP64 = 0, CQR2_OZAKI_BF16 = 1, CQR2_OZAKI_BF16_S6 = 2 } cqr2_precision_t;
 
 /* Plan flags. */
@@ -183,6 +197,13 @@ cqr2_status_t cqr2_selftest_wait_timeout(int64_t polls, void* stream);
 /* Synchronize the plan's stream and report the outcome of the last
  * factorization enqueued on the plan. */
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info);
+
+/* Slices per entry the plan's last factorization used: 0 for CQR2_FP64, 7
+ * for CQR2_OZAKI_BF16, and 6 or 7 for CQR2_OZAKI_BF16_S6 (7 when a column's
+ * crest ratio routed it, see cqr2_precision_t; 0 before its first
+ * factorization). Not part of the paper. Synchronizes the plan's stream;
+ * CQR2_ERR_INVALID_ARG for null arguments, CQR2_ERR_CUDA if the read fails. */
+cqr2_status_t cqr2_plan_split_slices(cqr2_plan_t plan, int32_t* slices);
 
 /* ---- Step-level entry points (each one step of Algorithm CQR on the
  * plan's m x n shape, on the plan's stream, asynchronous). ---- */

@@ -403,6 +403,13 @@ class Plan:
     def set_fused(self, fused: bool) -> None:
         cqr2_plan_set_fused(self.handle, fused)
 
+    def split_slices(self) -> int:
+        """Slices per entry of the last factorization (0 native FP64; 6 or 7
+        for a 6-slice plan, 7 when the device routed it to 7)."""
+        v = C.c_int32(0)
+        N.check(N.load().cqr2_plan_split_slices(self.handle, C.byref(v)), "cqr2_plan_split_slices")
+        return int(v.value)
+
     def set_stream(self, stream) -> None:
         N.check(N.load().cqr2_plan_set_stream(self.handle, _stream_handle(stream)), "cqr2_plan_set_stream")
 

@@ -74,7 +74,9 @@ struct cqr2_plan_st {
     int64_t ldq = 0;
   } hx;
   // split-precision (Ozaki) path
-  int oz_S = 0;  // slices per entry, 0 = native FP64
+  int oz_S = 0;     // slices per entry, 0 = native FP64
+  int oz_Scap = 0;  // slices the planes have room for (7 for a 6-slice plan, which may route to 7)
+  int* oz_gate = nullptr;  // device: slice count the current factorization uses (6-slice plans)
   unsigned short* oz_planes = nullptr;
   unsigned short* oz_rinv = nullptr;
   unsigned long long* oz_colmax = nullptr;
@@ -214,7 +216,7 @@ cqr2_status_t set_rows(cqr2_plan_st* p, int64_t m) {
   if (m == p->cm) return CQR2_OK;
   p->g = gram_geometry(m, (int)p->n, p->gram_cap, p->gram_cps);
   p->gemv_nsplit = gemv_splits(m, (int)p->n);
-  if (p->oz_S && ozaki_make_maps(p->oz_maps, m, (int)p->n, p->oz_S, p->oz_planes, p->oz_rinv) != cudaSuccess) {
+  if (p->oz_S && ozaki_make_maps(p->oz_maps, m, (int)p->n, p->oz_Scap, p->oz_planes, p->oz_rinv) != cudaSuccess) {
     p->cm = 0;
     return CQR2_ERR_CUDA;
   }
@@ -224,16 +226,33 @@ cqr2_status_t set_rows(cqr2_plan_st* p, int64_t m) {
 
 // Split-precision CholeskyQR2: the Gram and Q-forming contractions on the
 // BF16 tensor cores (Ozaki slices), CholInv and R2 R1 in native FP64.
+// A 6-slice plan routes on the device by the columns' crest ratios (scale
+// over root-mean-square, ozaki_route). Pass 1 runs its Gram with 6 slices
+// (that Gram only sets how well conditioned Q1 is), then checks A's columns
+// with the norms from W's diagonal; where a ratio is above 16 it re-slices A
+// with 7 slices for its Q-form. Pass 2 checks Q1's columns (unit norm) before
+// slicing, keeping an earlier 7, so its Gram -- which sets Q's orthogonality
+// -- and its Q-form use the chosen count. Both variants of each routed step
+// are launched and the one the gate does not select returns at once, so the
+// host never waits for the decision.
 cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
                                 int64_t ldr, int pass_base = 0) {
   const int n = (int)p->n, S = p->oz_S;
   const int64_t m = p->cm;
   cudaStream_t s = p->stream;
+  const bool route = S == 6;
+  const int* gate = route ? p->oz_gate : nullptr;
   if (!pass_base) TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
   TRY(hx_wait_input(p, s));
   // Up to OZAKI_FUSED_COLMAX_MAX_N columns the pass-1 Q-form also folds Q1's
   // column maxima into oz_colmax, so pass 2 skips the column-max sweep.
   const bool fused_cmax = n <= OZAKI_FUSED_COLMAX_MAX_N;
+  // launch a gated step for both slice counts (6-slice plans) or once
+  auto each = [&](auto&& step) -> cudaError_t {
+    if (!route) return step(S, (const int*)nullptr);
+    cudaError_t e = step(6, gate);
+    return e == cudaSuccess ? step(7, gate) : e;
+  };
   for (int pass = 1; pass <= 2; ++pass) {
     const double* X = pass == 1 ? dA : dQ;
     const int64_t ldx = pass == 1 ? lda : ldq;
@@ -244,11 +263,30 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
       } else {
         TRY(ozaki_colmax(X, ldx, m, n, p->oz_colmax, p->oz_cexp, s));
       }
-      TRY(ozaki_slice_cols(X, ldx, m, n, S, p->oz_cexp, p->oz_planes, s));
+      if (pass == 1 || !route) {
+        TRY(ozaki_slice_cols(X, ldx, m, n, S, p->oz_cexp, p->oz_planes, s));
+      } else {
+        TRY(ozaki_route(p->oz_cexp, nullptr, n, n, m, p->oz_gate, true, s));
+        TRY(each([&](int Sx, const int* g) {
+          return ozaki_slice_cols(X, ldx, m, n, Sx, p->oz_cexp, p->oz_planes, s, g);
+        }));
+      }
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_GRAM1 : CQR2_STAGE_GRAM2);
-      TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->oz_cap, p->W, n, p->st, s));
+      if (pass == 1 || !route) {
+        TRY(ozaki_gram(p->oz_maps, m, n, S, p->oz_cexp, p->oz_partial, p->oz_cap, p->W, n, p->st, s));
+      } else {
+        TRY(each([&](int Sx, const int* g) {
+          return ozaki_gram(p->oz_maps, m, n, Sx, p->oz_cexp, p->oz_partial, p->oz_cap, p->W, n, p->st, s, g);
+        }));
+      }
+    }
+    if (route && pass == 1) {
+      Stage st(p, CQR2_STAGE_SPLIT);
+      TRY(ozaki_route(p->oz_cexp, p->W, n, n, m, p->oz_gate, false, s));
+      // routed to 7: A again in 7 slices for this pass's Q-form
+      TRY(ozaki_slice_cols(X, ldx, m, n, 7, p->oz_cexp, p->oz_planes, s, gate));
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
@@ -257,14 +295,18 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, CQR2_STAGE_SPLIT);
-      TRY(ozaki_slice_rinv(p->Y, n, n, S, false, p->oz_cexp, p->oz_rinv, p->oz_fexp, s));
+      TRY(each([&](int Sx, const int* g) {
+        return ozaki_slice_rinv(p->Y, n, n, Sx, false, p->oz_cexp, p->oz_rinv, p->oz_fexp, s, g);
+      }));
     }
     {
       // The Q-form reads only the slices of X, so pass 2 may overwrite Q1 in place.
       Stage st(p, pass == 1 ? CQR2_STAGE_QFORM1 : CQR2_STAGE_QFORM2);
       const bool cm = pass == 1 && fused_cmax;
       if (cm) TRY(cudaMemsetAsync(p->oz_colmax, 0, (size_t)n * sizeof(unsigned long long), s));
-      TRY(ozaki_qform(p->oz_maps, m, n, S, p->oz_fexp, dQ, ldq, p->st, s, cm ? p->oz_colmax : nullptr));
+      TRY(each([&](int Sx, const int* g) {
+        return ozaki_qform(p->oz_maps, m, n, Sx, p->oz_fexp, dQ, ldq, p->st, s, cm ? p->oz_colmax : nullptr, g);
+      }));
     }
   }
   {
@@ -499,6 +541,7 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   if (oz_S) {
     og = ozaki_geometry(m, (int)n);
     p->oz_cap = ozaki_split_capacity(m, (int)n);
+    p->oz_Scap = oz_S == 6 ? 7 : oz_S;
     p->small = false;  // no m x n FP64 workspace: Q1 is staged in the output Q
     p->fused = false;
   }
@@ -524,11 +567,11 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
   take(nn);                                                          // 12 R0
   take(nn);                                                          // 13 Rt
   if (oz_S) {
-    take(ozaki_plane_elems(m, (int)n, oz_S) * 2);                    // 14 slice planes (bf16)
-    take((size_t)oz_S * n * og.np * 2);                              // 15 R^-1 planes
+    take(ozaki_plane_elems(m, (int)n, p->oz_Scap) * 2);              // 14 slice planes (bf16)
+    take((size_t)p->oz_Scap * n * og.np * 2);                        // 15 R^-1 planes
     take((size_t)n * sizeof(unsigned long long));                    // 16 column max
     take((size_t)n * sizeof(int));                                   // 17 column exponents
-    take(0);                                                         // 18 (unused)
+    take(sizeof(int));                                               // 18 slice-count gate
     take((size_t)n * sizeof(int));                                   // 19 R^-1 exponents
     take((size_t)p->oz_cap * n * n * sizeof(double));                // 20 Gram partials
   }
@@ -568,11 +611,13 @@ cqr2_status_t cqr2_plan_create(cqr2_plan_t* plan, int64_t m, int64_t n, int32_t 
     p->oz_colmax = reinterpret_cast<unsigned long long*>(p->ws + off[16]);
     p->oz_cexp = reinterpret_cast<int*>(p->ws + off[17]);
     p->oz_fexp = reinterpret_cast<int*>(p->ws + off[19]);
+    p->oz_gate = reinterpret_cast<int*>(p->ws + off[18]);
     p->oz_partial = at(20);
     // zero the planes once so that padding rows/columns read as zero
-    if (cudaMemsetAsync(p->oz_planes, 0, ozaki_plane_elems(m, (int)n, oz_S) * 2, p->stream) != cudaSuccess ||
-        cudaMemsetAsync(p->oz_rinv, 0, (size_t)oz_S * n * og.np * 2, p->stream) != cudaSuccess ||
-        ozaki_make_maps(p->oz_maps, m, (int)n, oz_S, p->oz_planes, p->oz_rinv) != cudaSuccess) {
+    if (cudaMemsetAsync(p->oz_planes, 0, ozaki_plane_elems(m, (int)n, p->oz_Scap) * 2, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->oz_rinv, 0, (size_t)p->oz_Scap * n * og.np * 2, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(p->oz_gate, 0, sizeof(int), p->stream) != cudaSuccess ||
+        ozaki_make_maps(p->oz_maps, m, (int)n, p->oz_Scap, p->oz_planes, p->oz_rinv) != cudaSuccess) {
       cudaGetLastError();
       cudaFreeHost(p->h_st);
       cudaFree(p->ws);
@@ -626,6 +671,20 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info) {
   if (!plan || !info) return CQR2_ERR_INVALID_ARG;
   return read_info(plan, info);
+}
+
+cqr2_status_t cqr2_plan_split_slices(cqr2_plan_t plan, int32_t* slices) {
+  if (!plan || !slices) return CQR2_ERR_INVALID_ARG;
+  if (plan->oz_S != 6) {
+    *slices = plan->oz_S;
+    return CQR2_OK;
+  }
+  int g = 0;
+  if (cudaMemcpyAsync(&g, plan->oz_gate, sizeof(int), cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess ||
+      cudaStreamSynchronize(plan->stream) != cudaSuccess)
+    return CQR2_ERR_CUDA;
+  *slices = g;
+  return CQR2_OK;
 }
 
 cqr2_status_t cqr2_factor_rows(cqr2_plan_t p, int64_t m, const double* dA, int64_t lda, double* dQ, int64_t ldq,

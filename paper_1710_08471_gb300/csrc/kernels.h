@@ -131,14 +131,17 @@ size_t ozaki_plane_elems(int64_t m, int n, int S);
 cudaError_t ozaki_make_maps(OzMaps& maps, int64_t m, int n, int S, void* planes, void* rinv_planes);
 cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned long long* colmax, int* cexp,
                          cudaStream_t s);
+// A non-null gate makes a launch do nothing unless *gate == S (device-side
+// routing of a 6-slice plan between 6 and 7 slices; see ozaki_route).
 cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int S, const int* cexp,
-                             unsigned short* planes, cudaStream_t s);
+                             unsigned short* planes, cudaStream_t s, const int* gate = nullptr);
 // R^-1 slices with X's column exponents cexp folded into its rows (cexp may be null).
 cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, const int* cexp,
-                             unsigned short* planes, int* fexp, cudaStream_t s);
+                             unsigned short* planes, int* fexp, cudaStream_t s, const int* gate = nullptr);
 // partial holds max_splits n x n blocks; a geometry needing more is refused.
 cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
-                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s);
+                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s,
+                       const int* gate = nullptr);
 // One thread waits on an mbarrier nothing arrives at (bounded, `polls`
 // polls) and records a timeout in *st, as the split-precision GEMM does.
 cudaError_t ozaki_selftest_wait(long long polls, DevStatus* st, cudaStream_t s);
@@ -146,7 +149,12 @@ cudaError_t ozaki_selftest_wait(long long polls, DevStatus* st, cudaStream_t s);
 // With colmax (zeroed by the caller) and n <= OZAKI_FUSED_COLMAX_MAX_N, the
 // column maxima of Q are folded into it as k_colmax would compute them.
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
-                        DevStatus* st, cudaStream_t s, unsigned long long* colmax = nullptr);
+                        DevStatus* st, cudaStream_t s, unsigned long long* colmax = nullptr,
+                        const int* gate = nullptr);
+// Sets *gate to 7 when some column's crest ratio sqrt(m) 2^cexp[j] / sqrt(W_jj)
+// exceeds 16 (or, with keep, when *gate is 7 already), else to 6.
+cudaError_t ozaki_route(const int* cexp, const double* W, int64_t ldw, int n, int64_t m, int* gate, bool keep,
+                        cudaStream_t s);
 constexpr int OZAKI_FUSED_COLMAX_MAX_N = 1024;
 // Column exponents from column maxima (the second half of ozaki_colmax).
 cudaError_t ozaki_exps(const unsigned long long* colmax, int n, int* cexp, cudaStream_t s);

@@ -45,6 +45,7 @@ namespace cqr2 {
 namespace {
 
 constexpr int OZ_BK = 64;          // contraction per K-block (128-byte rows)
+constexpr int OZ_QFORM_NA_MAX = 10;  // A ring slots of the Q-form (the Gram keeps 8)
 constexpr int OZ_BM = 128;         // tile rows
 constexpr int EXP_NONFINITE = OZ_EXP_NONFINITE;
 constexpr long long WAIT_LIMIT = 1ll << 24;
@@ -141,7 +142,8 @@ __global__ void k_exps_from_max(const unsigned long long* __restrict__ mx, int n
 template <int S>
 __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ X, int64_t ld, int64_t m, int n,
                                                     int64_t mp, const int* __restrict__ cexp,
-                                                    unsigned short* __restrict__ planes) {
+                                                    unsigned short* __restrict__ planes, const int* __restrict__ gate) {
+  if (gate && *gate != S) return;  // routed to the other slice count
   // four consecutive rows per thread: 32 contiguous bytes read, one 8-byte
   // store per slice (mp is a multiple of 64)
   const int j = blockIdx.y;
@@ -172,7 +174,9 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ X
 template <int S>
 __global__ void __launch_bounds__(256) k_slice_rinv(const double* __restrict__ Y, int64_t ldy, int n, int np,
                                                     bool from_upper, const int* __restrict__ cexp,
-                                                    unsigned short* __restrict__ planes, int* __restrict__ fexp) {
+                                                    unsigned short* __restrict__ planes, int* __restrict__ fexp,
+                                                    const int* __restrict__ gate) {
+  if (gate && *gate != S) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + warp;
   if (j >= n) return;
@@ -325,9 +329,12 @@ struct OzCfg {
   static constexpr int THREADS = 64 + 32 * EPI;                   // producer, MMA, epilogue warps
   static constexpr int A_BYTES = OZ_BM * OZ_BK * 2;               // one A slice tile
   static constexpr int B_BYTES = BN * OZ_BK * 2;                  // one B slice tile
-  static constexpr int NA = (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES < 8
-                                ? (227 * 1024 - 2048 - 2 * S * B_BYTES) / A_BYTES
-                                : 8;                              // A ring slots
+  // A ring slots: what shared memory leaves beside the B double buffer, the
+  // barriers and (Q-form) the column-max keys, at most 8 (Gram) or 10
+  static constexpr int RESERVED = BN == 32 ? 6200 : 2048, NA_CAP = BN == 32 ? OZ_QFORM_NA_MAX : 8;
+  static constexpr int NA = (227 * 1024 - RESERVED - 2 * S * B_BYTES) / A_BYTES < NA_CAP
+                                ? (227 * 1024 - RESERVED - 2 * S * B_BYTES) / A_BYTES
+                                : NA_CAP;
   static constexpr int CPT = BN * 4 * NGRP / EPI;                 // columns per epilogue thread
   static constexpr int TMAX = 256 / BN;                           // products per MMA (N <= 256)
   static constexpr int NBAR = 2 * NA + 4 + 2 * NBUF * S + 1;  // + the drain barrier
@@ -354,6 +361,9 @@ struct OzParams {
   // bit pattern of a value with the maximum's exponent, k_colmax's meaning)
   // are atomically folded in, so the next pass needs no column-max sweep
   unsigned long long* cmax;
+  // if set, the launch does nothing unless *gate equals its slice count (a
+  // plan routed between 6 and 7 slices launches both and one returns)
+  const int* gate;
 };
 constexpr int OZ_CMAX_N = OZAKI_FUSED_COLMAX_MAX_N;
 
@@ -464,6 +474,14 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
   tmem_ld16(taddr, w);
 }
 
+// TMEM load of 8 columns without the wait (the caller waits once for several).
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Drains group G of one chunk for this thread's CPT columns (16 at a time).
 template <int G, int CPT>
 __device__ __forceinline__ void oz_drain_group(uint32_t ta, long long* X, long long* Y) {
@@ -524,6 +542,7 @@ template <int S, int MODE, int BN, int EPI, int NGRP>
 __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
     k_ozaki_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzParams p) {
   using C = OzCfg<S, BN, EPI, NGRP>;
+  if (p.gate && *p.gate != S) return;  // uniform for the whole grid, before any barrier or TMEM
   constexpr int NA = C::NA, NBUF = C::NBUF, CPT = C::CPT;
   constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
   constexpr uint32_t ACC_COLS = S * BN;  // one accumulator buffer
@@ -775,13 +794,43 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       if (lane == 0) mbar_arrive(&accempty[ab * S + G]);                   \
     }                                                                      \
   }
-        OZ_DRAIN(0)
-        OZ_DRAIN(1)
-        OZ_DRAIN(2)
-        OZ_DRAIN(3)
-        OZ_DRAIN(4)
-        OZ_DRAIN(5)
-        OZ_DRAIN(6)
+        if (MODE == OZ_QFORM && CPT == 8) {
+          // two waits per chunk: groups 0-3 are complete once slice 3's
+          // commit has arrived (a commit tracks every earlier MMA), the rest
+          // once the last slice's has; all loads of a half share one wait
+#define OZ_HALF(G0, G1)                                                      \
+  if (ok) {                                                                  \
+    ok = mbar_wait(&accfull[ab * S + (G1)], par, p.st);                      \
+    if (ok) {                                                                \
+      asm volatile("tcgen05.fence::after_thread_sync;");                     \
+      uint32_t v[4][8];                                                      \
+      _Pragma("unroll") for (int g = G0; g <= G1; ++g) tmem_ld8_nw(ta + g * BN, v[g - G0]); \
+      tmem_wait_ld();                                                        \
+      asm volatile("tcgen05.fence::before_thread_sync;");                    \
+      __syncwarp();                                                          \
+      if (lane == 0)                                                         \
+        _Pragma("unroll") for (int g = G0; g <= G1; ++g) mbar_arrive(&accempty[ab * S + g]); \
+      if (G0 <= 0 && 0 <= G1) oz_accumulate<0, 8>(v[0 - G0], X, Y);         \
+      if (G0 <= 1 && 1 <= G1) oz_accumulate<1, 8>(v[1 - G0], X, Y);         \
+      if (G0 <= 2 && 2 <= G1) oz_accumulate<2, 8>(v[2 - G0], X, Y);         \
+      if (G0 <= 3 && 3 <= G1) oz_accumulate<3, 8>(v[3 - G0], X, Y);         \
+      if (G0 <= 4 && 4 <= G1) oz_accumulate<4, 8>(v[4 - G0 < 4 ? 4 - G0 : 0], X, Y); \
+      if (G0 <= 5 && 5 <= G1) oz_accumulate<5, 8>(v[5 - G0 < 4 ? 5 - G0 : 0], X, Y); \
+      if (G0 <= 6 && 6 <= G1) oz_accumulate<6, 8>(v[6 - G0 < 4 ? 6 - G0 : 0], X, Y); \
+    }                                                                        \
+  }
+          OZ_HALF(0, 3)
+          OZ_HALF(4, S - 1)
+#undef OZ_HALF
+        } else {
+          OZ_DRAIN(0)
+          OZ_DRAIN(1)
+          OZ_DRAIN(2)
+          OZ_DRAIN(3)
+          OZ_DRAIN(4)
+          OZ_DRAIN(5)
+          OZ_DRAIN(6)
+        }
 #undef OZ_DRAIN
       }
       if (!ok) break;
@@ -857,13 +906,42 @@ __global__ void k_selftest_wait(long long polls, DevStatus* st) {
 
 // Sum the split partials of the computed Gram tiles and mirror.
 __global__ void k_oz_gram_reduce(const double* __restrict__ partial, int nsplit, int n, double* __restrict__ W,
-                                 int64_t ldw) {
+                                 int64_t ldw, const int* __restrict__ gate, int S) {
+  if (gate && *gate != S) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= n || i > j) return;
   double s = 0.0;
   for (int b = 0; b < nsplit; ++b) s += partial[(int64_t)b * n * n + i + (int64_t)j * n];
   W[i + (int64_t)j * ldw] = s;
   W[j + (int64_t)i * ldw] = s;
+}
+
+// Slice-count routing of a 6-slice plan. A column's split keeps 7 + 8(S-1)
+// bits relative to its scale 2^e (the power of two above its largest entry),
+// so its normwise error grows with the crest ratio sqrt(m) 2^e / ||x_j||, the
+// scale over the column's root-mean-square (about 5 to 10 for Gaussian-like
+// columns). Where that ratio exceeds 2^OZ_ROUTE_LOG2_CREST for any column,
+// the gate is set to 7 and the rest of the factorization runs with 7 slices;
+// otherwise to 6. ||x_j||^2 is the diagonal of W = X^T X; with W null the
+// columns are taken to have unit norm (the second pass's X, Q1, has columns
+// of norm 1 up to the first pass's error). keep: an earlier 7 stays.
+constexpr double OZ_ROUTE_LOG2_CREST = 4.0;
+__global__ void k_oz_route(const int* __restrict__ cexp, const double* __restrict__ W, int64_t ldw, int n, int64_t m,
+                           int* __restrict__ gate, bool keep) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const double lm = log2((double)m);
+  int mine = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int e = cexp[j];
+    const double w = W ? W[j + (int64_t)j * ldw] : 1.0;
+    if (e >= EXP_NONFINITE || !(w > 0.0) || !(w < INFINITY)) continue;  // breakdown is reported elsewhere
+    if ((double)e + 0.5 * (lm - log2(w)) > OZ_ROUTE_LOG2_CREST) mine = 1;
+  }
+  if (mine) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *gate = (any || (keep && *gate == 7)) ? 7 : 6;
 }
 
 // ------------------------------------------------------------ host side
@@ -1002,28 +1080,28 @@ cudaError_t ozaki_colmax(const double* X, int64_t ld, int64_t m, int n, unsigned
 }
 
 cudaError_t ozaki_slice_cols(const double* X, int64_t ld, int64_t m, int n, int S, const int* cexp,
-                             unsigned short* planes, cudaStream_t s) {
+                             unsigned short* planes, cudaStream_t s, const int* gate) {
   const OzGeom g = ozaki_geometry(m, n);
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(g.mp, 4 * 256), 1024), (unsigned)n);
-  if (S == 7) k_slice_cols<7><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes);
-  else k_slice_cols<6><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes);
+  if (S == 7) k_slice_cols<7><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes, gate);
+  else k_slice_cols<6><<<grid, 256, 0, s>>>(X, ld, m, n, g.mp, cexp, planes, gate);
   count_launch();
   return cudaGetLastError();
 }
 
 
 cudaError_t ozaki_slice_rinv(const double* Y, int64_t ldy, int n, int S, bool from_upper, const int* cexp,
-                             unsigned short* planes, int* fexp, cudaStream_t s) {
+                             unsigned short* planes, int* fexp, cudaStream_t s, const int* gate) {
   const int np = (int)(ceil_div(n, OZ_BK) * OZ_BK);
   const unsigned grid = (unsigned)ceil_div(n, 8);
-  if (S == 7) k_slice_rinv<7><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp);
-  else k_slice_rinv<6><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp);
+  if (S == 7) k_slice_rinv<7><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp, gate);
+  else k_slice_rinv<6><<<grid, 256, 0, s>>>(Y, ldy, n, np, from_upper, cexp, planes, fexp, gate);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* cexp, double* partial,
-                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s) {
+                       int64_t max_splits, double* W, int64_t ldw, DevStatus* st, cudaStream_t s, const int* gate) {
   const OzGeom g = ozaki_geometry(m, n);
   if (g.nsplit > max_splits) return cudaErrorInvalidValue;
   OzParams p{};
@@ -1038,6 +1116,7 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
   p.st = st;
   p.ntiles = g.ntiles;
   p.nitems = (int64_t)g.ntiles * g.nsplit;
+  p.gate = gate;
   dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.col_a;
   const CUtensorMap& b = *(const CUtensorMap*)maps.col_b;
@@ -1045,13 +1124,13 @@ cudaError_t ozaki_gram(const OzMaps& maps, int64_t m, int n, int S, const int* c
                          : launch_oz<6, OZ_GRAM, OZ_GRAM_BN, OZ_GRAM_EPI, OZ_GRAM_GRP>(a, b, p, grid, s);
   if (e != cudaSuccess) return e;
   dim3 rg((unsigned)ceil_div(n, 128), (unsigned)n);
-  k_oz_gram_reduce<<<rg, 128, 0, s>>>(partial, g.nsplit, n, W, ldw);
+  k_oz_gram_reduce<<<rg, 128, 0, s>>>(partial, g.nsplit, n, W, ldw, gate, S);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* fexp, double* Q, int64_t ldq,
-                        DevStatus* st, cudaStream_t s, unsigned long long* colmax) {
+                        DevStatus* st, cudaStream_t s, unsigned long long* colmax, const int* gate) {
   const OzGeom g = ozaki_geometry(m, n);
   OzParams p{};
   p.cmax = n <= OZ_CMAX_N ? colmax : nullptr;
@@ -1065,11 +1144,19 @@ cudaError_t ozaki_qform(const OzMaps& maps, int64_t m, int n, int S, const int* 
   p.ntile_j = (int)ceil_div(n, OZ_QFORM_BN);
   p.ntiles = 1;
   p.nitems = (int64_t)p.ntile_j * ceil_div(m, OZ_BM);
+  p.gate = gate;
   dim3 grid((unsigned)std::min<int64_t>(p.nitems, sm_count_oz()));
   const CUtensorMap& a = *(const CUtensorMap*)maps.col_a_mn;
   const CUtensorMap& b = *(const CUtensorMap*)maps.rinv_b;
   return S == 7 ? launch_oz<7, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s)
                 : launch_oz<6, OZ_QFORM, OZ_QFORM_BN, OZ_QFORM_EPI, OZ_QFORM_GRP>(a, b, p, grid, s);
+}
+
+cudaError_t ozaki_route(const int* cexp, const double* W, int64_t ldw, int n, int64_t m, int* gate, bool keep,
+                        cudaStream_t s) {
+  k_oz_route<<<1, 256, 0, s>>>(cexp, W, ldw, n, m, gate, keep);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace cqr2

@@ -119,7 +119,15 @@ def test_ozaki_s6_cqr2(cq, kappa):
     A = synth.make_matrix(m, n, kappa, seed=17)
     with cq.Plan(m, n, precision=cq.CQR2_OZAKI_BF16_S6) as p:
         Q, R, info = p.factor(to_dev(A))
+        # Gaussian-like columns (crest ratio about 5 to 10): no routing
+        assert p.split_slices() == 6
     _check(A, to_host(Q), to_host(R), kappa)
+    with cq.Plan(m, n, precision=cq.CQR2_OZAKI_BF16) as p:
+        p.factor(to_dev(A))
+        assert p.split_slices() == 7
+    with cq.Plan(m, n) as p:
+        p.factor(to_dev(A))
+        assert p.split_slices() == 0
 
 
 def test_ozaki_deterministic_and_matches_fp64_closely(cq):

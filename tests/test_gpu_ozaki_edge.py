@@ -11,6 +11,11 @@ inputs here are the ones where that choice shows:
 * one entry of a column 1e8 times the column's median (synth.spiked_column);
 * a column of entries 1e-20 next to O(1) columns (synth.scaled_column).
 
+A 6-slice plan routes itself to 7 slices on the device when a column's crest
+ratio sqrt(m) 2^e_j / ||x_j|| exceeds 16 (in either pass); the test checks
+that it did so exactly for the inputs whose crest ratios (of A, and of the
+oracle's Q1 for the second pass) exceed 16.
+
 Each runs through CQR2_OZAKI_BF16 (S = 7) and CQR2_OZAKI_BF16_S6 end to end at
 ten times the FP64 tolerances (orthogonality <= max(1e-11, 10x the oracle's),
 residual <= max(1e-12, 10x the oracle's), R relative <= 1e-11 kappa with kappa
@@ -66,6 +71,13 @@ def _inputs():
 CASES = sorted(_inputs())
 
 
+def _max_crest(X):
+    """Largest sqrt(m) 2^e_j / ||x_j|| over the columns (2^e_j the power of
+    two above the column's largest magnitude)."""
+    m = X.shape[0]
+    return float(np.max(pow2_above(np.max(np.abs(X), axis=0)) * np.sqrt(m) / np.linalg.norm(X, axis=0)))
+
+
 def _kappa_equilibrated(A):
     c = np.linalg.norm(A, axis=0)
     return float(np.linalg.cond(A / c[None, :]))
@@ -80,9 +92,12 @@ def test_ozaki_edge_cqr2(cq, case, prec):
     assert k < 1e7
     with cq.Plan(m, n, precision=prec) as p:
         Q, R, info = p.factor(to_dev(A))
+        used = p.split_slices()
     assert info.status == 0
     Q, R = to_host(Q), to_host(R)
-    Qo, Ro = oracle.cqr2(A)
+    Qo, Ro, inter = oracle.cqr2(A, keep=True)
+    crest = max(_max_crest(A), _max_crest(inter["Q1"]))
+    assert used == (7 if prec == 1 or crest > 16 else 6), (used, crest)
     orth = oracle.orthogonality(Q)
     res = oracle.residual(A, Q, R)
     assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
