@@ -14,6 +14,7 @@ from .cholqr2 import (  # noqa: F401
     lstsq,
     nominal_flops,
     orthogonality,
+    panel_cqr2,
     rel_error,
     residual,
     right_solve,

@@ -15,6 +15,9 @@ and notation, with numpy FP64 (IEEE round-to-nearest) arithmetic:
   Q = A R^-1.
 * CQR2    (Algorithm CQR2, Section II-E): (Q1, R1) = CQR(A); (Q, R2) = CQR(Q1);
   R = R2 R1.
+* Panels (the subpanel variant Section V names as future work): CQR2 of each
+  column panel after two block projections against the earlier panels
+  (panel_cqr2).
 * Inverse depth (Section III-A's triangular inverted blocks, the InverseDepth
   parameter of Section IV): CholInv forms the inverse only for the diagonal
   blocks below the top `depth` halvings; L21 and Q come from block forward
@@ -214,6 +217,47 @@ def cqr2(A: np.ndarray, keep: bool = False, inverse_depth: int = 0):
     for k, v in i2.items():
         info[k + "2"] = v
     return Q, R, info
+
+
+def panel_cqr2(A: np.ndarray, b: int, keep: bool = False):
+    """CholeskyQR2 on column panels of width b: the reading of the paper's
+    future-work variant that operates on subpanels (Section V, Conclusion).
+
+    Left to right, panel k (columns c0 .. c0 + b - 1) is projected twice
+    against the finished panels Q_<k -- C = Q_<k^T V, V = V - Q_<k C; the
+    second pass reorthogonalises, as block Gram-Schmidt needs -- and then
+    factored by CQR2 (Algorithm CQR2): V = Q_k R_kk. R's block above the
+    diagonal block is the sum of the two projections' coefficients. With
+    b >= n this is CQR2 itself. Raises PassFailed with the pivot as a column
+    index of A when a panel's CholeskyQR2 breaks down.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if m < n or n < 1 or b < 1:
+        raise ValueError("panel CQR2 needs m >= n >= 1 and b >= 1")
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    coeffs = []
+    for c0 in range(0, n, b):
+        c1 = min(n, c0 + b)
+        V = A[:, c0:c1].copy()
+        if c0:
+            Qp = Q[:, :c0]
+            for _ in range(2):  # projection, then reorthogonalisation
+                C = Qp.T @ V
+                V = V - Qp @ C
+                R[:c0, c0:c1] += C
+                coeffs.append(C)
+        try:
+            Qk, Rk = cqr2(V)
+        except PassFailed as e:
+            err = PassFailed(e.pass_no, NotSPD(e.pivot + c0, e.value))
+            raise err from None
+        Q[:, c0:c1] = Qk
+        R[c0:c1, c0:c1] = Rk
+    if keep:
+        return Q, R, dict(coeffs=coeffs)
+    return Q, R
 
 
 UNIT_ROUNDOFF = 2.0 ** -53

@@ -552,3 +552,78 @@ def test_yardstick_pins_accept_oracle():
 @pytest.mark.parametrize("key", sorted(_YARDSTICK_MUTATIONS))
 def test_yardstick_pins_reject_planted_mistake(key):
     assert not _yardstick_pins_pass(_yardstick_mutant(key))
+
+
+# ------------------------------- CholeskyQR2 on column panels (Section V)
+
+@pytest.mark.parametrize("m,n,b,kappa", [(600, 96, 32, 1e3), (1500, 300, 128, 1e5), (2048, 512, 128, 1e6),
+                                         (400, 50, 1, 1e2), (777, 130, 64, 1e4)])
+def test_panel_cqr2_matches_householder(m, n, b, kappa):
+    A = synth.make_matrix(m, n, kappa, seed=51)
+    Q, R = oracle.panel_cqr2(A, b)
+    Qh, Rh = oracle.householder_qr(A)
+    tol = 10 * n * kappa * EPS
+    assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
+    assert oracle.rel_error(R, Rh) <= tol
+    assert np.linalg.norm(Q - Qh) / math.sqrt(n) <= tol
+    # the reorthogonalised projections keep Q orthonormal to working accuracy
+    assert oracle.orthogonality(Q) <= 100 * n * EPS
+    assert oracle.residual(A, Q, R) <= 100 * n * EPS
+
+
+def test_panel_cqr2_one_panel_is_cqr2():
+    A = synth.make_matrix(500, 40, 1e4, seed=52)
+    for b in (40, 64, 1000):
+        Q, R = oracle.panel_cqr2(A, b)
+        Qc, Rc = oracle.cqr2(A)
+        np.testing.assert_array_equal(Q, Qc)
+        np.testing.assert_array_equal(R, Rc)
+
+
+def test_panel_cqr2_breakdown_reports_column_of_A():
+    A = synth.make_matrix(1000, 200, 1e2, seed=53)
+    A[:, 150] = 0.0  # panel 2 of width 64 (columns 128..191)
+    with pytest.raises(oracle.PassFailed) as e:
+        oracle.panel_cqr2(A, 64)
+    assert e.value.pass_no == 1 and e.value.pivot == 150
+
+
+_PANEL_MUTATIONS = {
+    "panel_no_reorthogonalisation": ("            for _ in range(2):  # projection, then reorthogonalisation",
+                                     "            for _ in range(1):  # projection, then reorthogonalisation"),
+    "panel_coefficients_overwritten": ("                R[:c0, c0:c1] += C", "                R[:c0, c0:c1] = C"),
+    "panel_pivot_not_shifted": ("NotSPD(e.pivot + c0, e.value)", "NotSPD(e.pivot, e.value)"),
+}
+
+
+def _panel_pins_pass(mod) -> bool:
+    try:
+        A = synth.make_matrix(2048, 512, 1e6, seed=54)
+        Q, R = mod.panel_cqr2(A, 128)
+        Qh, Rh = oracle.householder_qr(A)
+        if not (oracle.orthogonality(Q) <= 100 * 512 * EPS and oracle.residual(A, Q, R) <= 100 * 512 * EPS
+                and oracle.rel_error(R, Rh) <= 10 * 512 * 1e6 * EPS):
+            return False
+        B = synth.make_matrix(1000, 200, 1e2, seed=53)
+        B[:, 150] = 0.0
+        try:
+            mod.panel_cqr2(B, 64)
+            return False
+        except mod.PassFailed as e:
+            return e.pivot == 150
+    except Exception:
+        return False
+
+
+def test_panel_pins_accept_oracle():
+    assert _panel_pins_pass(ocq)
+
+
+@pytest.mark.parametrize("key", sorted(_PANEL_MUTATIONS))
+def test_panel_pins_reject_planted_mistake(key):
+    src = inspect.getsource(ocq)
+    old, new = _PANEL_MUTATIONS[key]
+    assert src.count(old) == 1, key
+    mod = types.ModuleType(f"oracle_mutant_{key}")
+    exec(compile(src.replace(old, new), f"<mutant {key}>", "exec"), mod.__dict__)
+    assert not _panel_pins_pass(mod)
