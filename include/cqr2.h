@@ -183,6 +183,29 @@ cqr2_status_t cqr2_plan_set_fused(cqr2_plan_t plan, int32_t fused);
  * has a call in flight. */
 cqr2_status_t cqr2_plan_set_inverse_depth(cqr2_plan_t plan, int32_t depth);
 
+/* CholeskyQR2 on column panels of width b (the paper's conclusion, Section
+ * V, names a CholeskyQR2 that operates on subpanels, to cut the extra
+ * computation on near-square matrices, as future work; this is the library's
+ * reading of it). With 1 <= b < n, cqr2_factor (and the _rows, _host and
+ * least-squares forms) factors A panel by panel, left to right: panel k's
+ * columns are copied to their place in Q, projected twice against the
+ * panels before it (C = Q_<k^T V, V -= Q_<k C; the second projection
+ * reorthogonalises), and factored in place by CholeskyQR2, which gives its
+ * columns of Q and R's diagonal block; R's block above it is the sum of the
+ * two projections' coefficients. CholInv then works on b x b Gram matrices
+ * only, where plain CholeskyQR2 factors and inverts two n x n ones and forms
+ * R2 R1. The same factorization up to rounding; accurate while each
+ * projected panel satisfies CholeskyQR2's own condition (its condition
+ * number well below 1e8). A breakdown reports the pass of the panel's
+ * CholeskyQR2 and the pivot as a column index of A.
+ * b = 0 or b >= n turns it off (plain CholeskyQR2). Native-FP64 plans
+ * without CQR2_SHIFTED only (else CQR2_ERR_UNSUPPORTED); b < 0 is
+ * CQR2_ERR_INVALID_ARG. Allocates the panels' own plans (m x b, and the
+ * narrower last panel) and n x b doubles (CQR2_ERR_OOM on failure);
+ * synchronizes the plan's stream; not for use while the plan has a call in
+ * flight. */
+cqr2_status_t cqr2_plan_set_panel_width(cqr2_plan_t plan, int64_t b);
+
 /* Self-test of the bounded-wait timeout path (no counterpart in the paper):
  * runs one thread that waits, with the library's bounded mbarrier wait, on a
  * barrier that nothing arrives at, for at most `polls` polls (1..2^24), and

@@ -403,6 +403,10 @@ class Plan:
     def set_fused(self, fused: bool) -> None:
         cqr2_plan_set_fused(self.handle, fused)
 
+    def set_panel_width(self, b: int) -> None:
+        """Factor on column panels of width b (0 = plain CholeskyQR2)."""
+        N.check(N.load().cqr2_plan_set_panel_width(self.handle, int(b)), "cqr2_plan_set_panel_width")
+
     def split_slices(self) -> int:
         """Slices per entry of the last factorization (0 native FP64; 6 or 7
         for a 6-slice plan, 7 when the device routed it to 7)."""

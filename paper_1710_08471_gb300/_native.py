@@ -67,6 +67,7 @@ SIGNATURES = {
     "cqr2_lstsq_rows": (C.c_int, [_P, _I64, _D, _I64, _D, _D, _D, _I64, _D, _I64, C.POINTER(Info)]),
     "cqr2_plan_info": (C.c_int, [_P, C.POINTER(Info)]),
     "cqr2_plan_split_slices": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "cqr2_plan_set_panel_width": (C.c_int, [_P, _I64]),
     "cqr2_plan_set_gram_ctas": (C.c_int, [_P, C.c_int32]),
     "cqr2_plan_set_fused": (C.c_int, [_P, C.c_int32]),
     "cqr2_plan_set_inverse_depth": (C.c_int, [_P, C.c_int32]),

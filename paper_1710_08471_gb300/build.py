@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(LIBDIR, "libcqr2.so")
 
 SOURCES = ["api.cu", "gram.cu", "qform.cu", "gemm.cu", "cholinv.cu", "lstsq.cu", "ozaki.cu", "batched.cu",
-           "batch_api.cu"]
+           "batch_api.cu", "panels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -24,6 +24,13 @@ struct cqr2_plan_st {
   int gram_cps = 4;      // Gram CTAs per SM (autotuned knob, 1..GRAM_CPS_MAX)
   int64_t gram_cap = 0;  // row ranges the Gram partials have room for (any cm <= m)
   int inv_depth = 0;         // CholInv levels without Y21 (0: whole inverse)
+  // CholeskyQR2 on column panels of width panel_b (0: off): plans for the
+  // panels' own CholeskyQR2 (width panel_b, and the narrower last panel) and
+  // n x panel_b doubles for the second projection's coefficients
+  int64_t panel_b = 0;
+  cqr2_plan_st* pan_full = nullptr;
+  cqr2_plan_st* pan_tail = nullptr;
+  double* pan_C = nullptr;
   double* Tsolve = nullptr;  // block-substitution scratch, ldt x right_solve_temp_cols(n)
   double* skws = nullptr;    // split-k scratch of CholInv's small products
   int64_t ldt = 0;
@@ -424,7 +431,52 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
 // pass (W = A^T A + s I, [L0, Y0] = CholInv(W), Q0 = A Y0^T staged in Q),
 // CholeskyQR2 of Q0 in place (its passes report as 2 and 3), R = R' R0.
 cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                         int64_t ldr);
+
+// CholeskyQR2 on column panels (Section V names a CholeskyQR2 that works on
+// subpanels, to cut the extra computation near-square matrices cost, as
+// future work; this is the library's reading of it). Left to right, each
+// panel of b columns is copied into its place in Q, projected twice against
+// the panels before it (block Gram-Schmidt with one reorthogonalisation:
+// C = Q_<k^T V, V -= Q_<k C, twice, R's block above the diagonal gets the sum
+// of both C), and factored by CholeskyQR2 in place, which gives its Q columns
+// and R's diagonal block. CholInv then only ever sees b x b Gram matrices,
+// instead of the whole n x n ones (twice) and R2 R1 of plain CQR2.
+cqr2_status_t factor_panels(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
+                            int64_t ldr) {
+  const int64_t n = p->n, m = p->cm, b = p->panel_b;
+  cudaStream_t s = p->stream;
+  TRY(cudaMemsetAsync(p->st, 0, sizeof(DevStatus), s));
+  TRY(hx_wait_input(p, s));
+  // R's strictly lower part stays zero; its blocks are written panel by panel
+  TRY(cudaMemset2DAsync(dR, (size_t)ldr * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s));
+  for (int64_t c0 = 0; c0 < n; c0 += b) {
+    const int64_t bk = std::min(b, n - c0);
+    cqr2_plan_st* in = bk == b ? p->pan_full : p->pan_tail;
+    double* Qk = dQ + c0 * ldq;
+    if (dQ != dA) TRY(copy_cols(Qk, ldq, dA + c0 * lda, lda, m, bk, cudaMemcpyDeviceToDevice, s));
+    if (c0 > 0) {
+      double* Rk = dR + c0 * ldr;  // R(0:c0, c0:c0+bk)
+      TRY(gemm_f64(c0, bk, m, 1.0, dQ, ldq, Qk, ldq, 0.0, Rk, ldr, GEMM_TA | GEMM_BETA0, s, p->skws,
+                   cholinv_splitk_doubles()));
+      TRY(gemm_f64(m, bk, c0, -1.0, dQ, ldq, Rk, ldr, 1.0, Qk, ldq, 0, s));
+      TRY(gemm_f64(c0, bk, m, 1.0, dQ, ldq, Qk, ldq, 0.0, p->pan_C, c0, GEMM_TA | GEMM_BETA0, s, p->skws,
+                   cholinv_splitk_doubles()));
+      TRY(gemm_f64(m, bk, c0, -1.0, dQ, ldq, p->pan_C, c0, 1.0, Qk, ldq, 0, s));
+      TRY(add_block(p->pan_C, c0, Rk, ldr, c0, bk, s));
+    }
+    in->stream = s;
+    cqr2_status_t r = set_rows(in, m);
+    if (r != CQR2_OK) return r;
+    if ((r = factor_any(in, Qk, ldq, Qk, ldq, dR + c0 + c0 * ldr, ldr)) != CQR2_OK) return r;
+    TRY(status_merge(p->st, in->st, c0, s));
+  }
+  return CQR2_OK;
+}
+
+cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double* dQ, int64_t ldq, double* dR,
                          int64_t ldr) {
+  if (p->panel_b) return factor_panels(p, dA, lda, dQ, ldq, dR, ldr);
   if (!(p->flags & CQR2_SHIFTED)) return factor_impl(p, dA, lda, dQ, ldq, dR, ldr, 0);
   const int n = (int)p->n;
   const int64_t m = p->cm;
@@ -649,6 +701,9 @@ cqr2_status_t cqr2_plan_set_stream(cqr2_plan_t plan, void* stream) {
 void cqr2_plan_destroy(cqr2_plan_t plan) {
   if (!plan) return;
   cudaStreamSynchronize(plan->stream);
+  cqr2_plan_destroy(plan->pan_full);
+  cqr2_plan_destroy(plan->pan_tail);
+  cudaFree(plan->pan_C);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
@@ -671,6 +726,46 @@ void cqr2_plan_destroy(cqr2_plan_t plan) {
 cqr2_status_t cqr2_plan_info(cqr2_plan_t plan, cqr2_info_t* info) {
   if (!plan || !info) return CQR2_ERR_INVALID_ARG;
   return read_info(plan, info);
+}
+
+cqr2_status_t cqr2_plan_set_panel_width(cqr2_plan_t p, int64_t b) {
+  if (!p || b < 0) return CQR2_ERR_INVALID_ARG;
+  if (b > 0 && b < p->n && (p->oz_S || (p->flags & CQR2_SHIFTED))) return CQR2_ERR_UNSUPPORTED;
+  if (check_device(p) != CQR2_OK) return CQR2_ERR_INVALID_ARG;
+  if (b >= p->n) b = 0;  // one panel is plain CholeskyQR2
+  if (b == p->panel_b) return CQR2_OK;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return CQR2_ERR_CUDA;
+  cqr2_plan_destroy(p->pan_full);
+  cqr2_plan_destroy(p->pan_tail);
+  cudaFree(p->pan_C);
+  p->pan_full = p->pan_tail = nullptr;
+  p->pan_C = nullptr;
+  p->panel_b = 0;
+  if (b == 0) return CQR2_OK;
+  const int64_t tail = p->n % b;
+  const uint32_t fl = CQR2_INPLACE | CQR2_FUSED;
+  cqr2_status_t r = cqr2_plan_create(&p->pan_full, p->m, b, CQR2_FP64, fl, p->stream);
+  if (r == CQR2_OK && tail) r = cqr2_plan_create(&p->pan_tail, p->m, tail, CQR2_FP64, fl, p->stream);
+  if (r == CQR2_OK && cudaMalloc(&p->pan_C, (size_t)p->n * b * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    r = CQR2_ERR_OOM;
+  }
+  if (r != CQR2_OK) {
+    cqr2_plan_destroy(p->pan_full);
+    cqr2_plan_destroy(p->pan_tail);
+    cudaFree(p->pan_C);
+    p->pan_full = p->pan_tail = nullptr;
+    p->pan_C = nullptr;
+    return r;
+  }
+  if (p->gexec) {  // a captured graph of the unpaneled sequence no longer applies
+    cudaGraphExecDestroy(p->gexec);
+    cudaGraphDestroy(p->graph);
+    p->gexec = nullptr;
+    p->graph = nullptr;
+  }
+  p->panel_b = b;
+  return CQR2_OK;
 }
 
 cqr2_status_t cqr2_plan_split_slices(cqr2_plan_t plan, int32_t* slices) {

@@ -184,6 +184,14 @@ size_t batched_small_smem();
 cudaError_t cqr2_small_batched(const BatchProblem* probs, int count, int* next, BatchStatus* status,
                                cudaStream_t s);
 
+// ---------------------------------------------------------------- panels
+// B(0:rows, 0:cols) += A(0:rows, 0:cols).
+cudaError_t add_block(const double* A, int64_t lda, double* B, int64_t ldb, int64_t rows, int64_t cols,
+                      cudaStream_t s);
+// Copies a panel's first breakdown (status word `inner`) into `outer`, unless
+// outer holds one already, with the pivot index shifted by col0.
+cudaError_t status_merge(DevStatus* outer, const DevStatus* inner, int64_t col0, cudaStream_t s);
+
 // ---------------------------------------------------------------- lstsq
 // c = Q^T b as split-m partials, then x solves R x = c (back substitution).
 int64_t gemv_splits(int64_t m, int n);
