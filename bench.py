@@ -574,6 +574,7 @@ def bench_configs(steps: int, warmup: int, local: int, peaks: dict, clk: dict, s
       L2 rewritten between steps (its 2 MB input fits in L2);
     - wide512 (2^21 x 512, kappa 1e6), native FP64 and split precision (S = 7)
       at the same shape;
+    - 8192 x 4096 (kappa 1e4), plain CholeskyQR2 against column panels of 512;
     - batch (1024 problems of 4096 x 32 in one grouped launch per step);
     - the 20,000-request least-squares stream at 2000 requests/s, split
       precision, continuous batching against one request at a time."""
@@ -669,6 +670,37 @@ def bench_configs(steps: int, warmup: int, local: int, peaks: dict, clk: dict, s
         del A, Q, R, hA
     except Exception as ex:
         out["wide512"] = {"error": repr(ex)}
+    torch.cuda.empty_cache()
+
+    # ---- near-square: 8192 x 4096, plain CholeskyQR2 against panels of 512
+    try:
+        m, n, kappa, b = 8192, 4096, 1e4, 512
+        hA = synth.make_matrix(m, n, kappa, 6)
+        A = cq.colmajor(torch.from_numpy(np.ascontiguousarray(hA.T)).to(dev).t())
+        Q, R = cq.empty_colmajor(m, n, device=dev), cq.empty_colmajor(n, n, device=dev)
+        stream = torch.cuda.current_stream()
+        fl = nominal_flops(m, n)
+        res = {"workload": "FP64 CholeskyQR2, m=8192 n=4096 (268 MB), kappa=1e4, plain and on column panels",
+               "m": m, "n": n, "kappa": kappa, "panel_width": b,
+               "l2": "inputs 268 MB > 129 MB L2 (no flush)"}
+        t0 = time.perf_counter()
+        Qo, Ro = oracle.panel_cqr2(hA, b)
+        res["cpu_baseline"] = {"value": fl / (time.perf_counter() - t0) / 1e12, "unit": "TFLOP/s",
+                               "cores": cpu_cores(), "kind": "oracle", "sample": "full workload, panels, one run"}
+        for name, width in (("plain", 0), ("panels", b)):
+            with cq.Plan(m, n, stream=stream) as pl:
+                pl.set_panel_width(width)
+                ms, launches, st = timed_plan(pl, A, Q, R, stream, max(3, min(steps, 5)), warmup, True)
+            e = errs(hA, Q, R, Ro)
+            res[name] = {"ms_per_step": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                         "vs_fp64_peak": fl / (ms * 1e-3) / 1e12 / fp64_peak(clk),
+                         "stages_ms": {k: round(v, 3) for k, v in st.items()}, "errors": e}
+        res["oracle"] = {"orthogonality": oracle.orthogonality(Qo), "residual": oracle.residual(hA, Qo, Ro)}
+        res["panel_speedup"] = res["plain"]["ms_per_step"] / res["panels"]["ms_per_step"]
+        out["panels"] = res
+        del A, Q, R, hA, Qo
+    except Exception as ex:
+        out["panels"] = {"error": repr(ex)}
     torch.cuda.empty_cache()
 
     # ---- batch: 1024 problems of 4096 x 32 per grouped launch

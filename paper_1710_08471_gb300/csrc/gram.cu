@@ -159,25 +159,41 @@ __global__ void __launch_bounds__(NT) k_gram_tile(const double* __restrict__ A, 
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ partial, int64_t nsplit, int T, int ntile,
-                              int ntiles_total, int n, double* __restrict__ W, int64_t ldw) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// W = the sum of the row ranges' partial tiles, mirrored. The ranges are cut
+// into RC contiguous chunks: warp c of a block sums chunk c for 32 elements
+// of one column, in range order, and thread c = 0 adds the chunk sums in
+// chunk order -- the same fixed order on every call (deterministic), with RC
+// warps sharing each element's long sum (the FP64 pipe charges every warp
+// instruction in full, so one thread per element and hundreds of ranges left
+// most of the GPU idle).
+constexpr int GRAM_RC = 8;
+__global__ void __launch_bounds__(32 * GRAM_RC) k_gram_reduce(const double* __restrict__ partial, int64_t nsplit,
+                                                              int T, int ntile, int ntiles_total, int n,
+                                                              double* __restrict__ W, int64_t ldw) {
+  __shared__ double part[GRAM_RC][32];
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   const int j = blockIdx.y;
-  if (i >= n || i > j) return;
-  const int I = i / T, Jt = j / T;
-  int tile;
-  if (I == Jt) {
-    tile = I;
-  } else {
-    tile = ntile + I * ntile - I * (I + 1) / 2 + (Jt - I - 1);
-  }
-  const int64_t loc = (i - I * T) + (int64_t)(j - Jt * T) * T;
-  const int64_t stride = (int64_t)ntiles_total * T * T;
-  const double* p = partial + (int64_t)tile * T * T + loc;
+  const bool live = i < n && i <= j;
   double s = 0.0;
-  for (int64_t b = 0; b < nsplit; ++b) s += p[b * stride];
-  W[i + (int64_t)j * ldw] = s;
-  W[j + (int64_t)i * ldw] = s;
+  if (live) {
+    const int I = i / T, Jt = j / T;
+    const int tile = I == Jt ? I : ntile + I * ntile - I * (I + 1) / 2 + (Jt - I - 1);
+    const int64_t loc = (i - I * T) + (int64_t)(j - Jt * T) * T;
+    const int64_t stride = (int64_t)ntiles_total * T * T;
+    const double* p = partial + (int64_t)tile * T * T + loc;
+    const int64_t b0 = nsplit * c / GRAM_RC, b1 = nsplit * (c + 1) / GRAM_RC;
+    for (int64_t b = b0; b < b1; ++b) s += p[b * stride];
+  }
+  part[c][lane] = s;
+  __syncthreads();
+  if (c == 0 && live) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int k = 1; k < GRAM_RC; ++k) t += part[k][lane];
+    W[i + (int64_t)j * ldw] = t;
+    W[j + (int64_t)i * ldw] = t;
+  }
 }
 
 template <int T, int NT, bool DIAG>
@@ -239,8 +255,8 @@ cudaError_t gram_partials(const double* A, int64_t lda, int64_t m, int n, const 
 }
 
 cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double* W, int64_t ldw, cudaStream_t s) {
-  dim3 block(128);
-  dim3 grid((unsigned)ceil_div(n, 128), (unsigned)n);
+  dim3 block(32 * GRAM_RC);
+  dim3 grid((unsigned)ceil_div(n, 32), (unsigned)n);
   k_gram_reduce<<<grid, block, 0, s>>>(partial, g.nsplit, g.T, g.ntile, g.ntiles_total, n, W, ldw);
   count_launch();
   return cudaGetLastError();
