@@ -64,10 +64,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@438bba48f733e7ec": 2938563328,
-    "k_ozaki_gemm<7,QFORM>@tall@438bba48f733e7ec": 23508506624,
-    "k_ozaki_gemm<7,GRAM>@mid@438bba48f733e7ec": 1892568064,
-    "k_ozaki_gemm<7,GRAM>@tall@438bba48f733e7ec": 15140544512,
+    "k_ozaki_gemm<7,QFORM>@mid@7f16f198549a7344": 2938854912,
+    "k_ozaki_gemm<7,QFORM>@tall@7f16f198549a7344": 23510839296,
+    "k_ozaki_gemm<7,GRAM>@mid@7f16f198549a7344": 1892679424,
+    "k_ozaki_gemm<7,GRAM>@tall@7f16f198549a7344": 15141435392,
     "k_cqr2_small_batched@batch@c56aa36f0d944e5a": 5306968320,
 }
 
@@ -567,6 +567,29 @@ def oracle_seconds_one_core(m: int, n: int, kappa, seed: int, repeats: int = 5) 
         return None
 
 
+def fp64_gemm_probe(dev) -> dict:
+    """A measured FP64 reference beside the derived DFMA peak: cuBLAS DGEMM
+    (torch.matmul, float64) on 8192 x 8192 operands, best of 3 after one
+    warm-up, CUDA events."""
+    import torch
+
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    torch.cuda.empty_cache()
+    return {"cublas_dgemm_tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "n": n, "ms": best}
+
+
 def bench_configs(steps: int, warmup: int, local: int, peaks: dict, clk: dict, serving_pool=None) -> dict:
     """The other configurations of the benchmark plan, measured in the same
     run (device-timed with CUDA events, errors against the CPU oracle):
@@ -785,6 +808,13 @@ def bench_ours(args, ws, rank, local):
     if rank == 0 and not args.quick:
         import oracle
 
+        try:
+            probe = fp64_gemm_probe(dev)
+            probe["frac_of_derived_peak"] = probe["cublas_dgemm_tflops"] / fp64_pk
+            out["fp64_reference"] = probe
+            out["vs_fp64_peak"]["frac_of_cublas_dgemm"] = value / ws / probe["cublas_dgemm_tflops"]
+        except Exception as ex:  # a reference probe must not cost the main line
+            out["fp64_reference"] = {"error": repr(ex)}
         hQ, hQ_t = pinned_colmajor(m, n)
         hR, hR_t = pinned_colmajor(n, n)
         # End to end through the host-buffer C entry point, before the CPU
