@@ -40,15 +40,15 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   __syncthreads();
   // Right-looking Cholesky with the right-looking inverse interleaved, and a
   // look-ahead of one pivot. GB300 issues an FP64 warp instruction at a small
-  // fraction of the FP32 rate, and the pivots are a serial chain, so step k
-  // runs in two phases:
-  //   1. column k of L and row k of Y = L^-1 are scaled by 1/l_kk;
-  //   2. warp 0 applies step k to column k+1 and then forms pivot k+1 (its
-  //      square root and reciprocal from a short Newton sequence), while the
-  //      other warps apply step k to the rest of the trailing matrix and to
-  //      the rows of Y below k.
-  // Every element sees the same operations in the same order as the plain
-  // factorization followed by the plain inverse.
+  // fraction of the FP32 rate, and the pivots are a serial chain, so in step k
+  // (column k of L and row k of Y = L^-1 already final)
+  //   - warp 0 applies step k to column k+1 of L and row k+1 of Y, forms pivot
+  //     k+1 (its square root and reciprocal from a short Newton sequence) and
+  //     scales that column and row by 1/l_(k+1,k+1);
+  //   - the other warps apply step k to the rest of the trailing matrix and to
+  //     the rows of Y below k+1;
+  // with one block barrier per step. Every element sees the same operations in
+  // the same order as the plain factorization followed by the plain inverse.
   __shared__ double rdiag[NB];
   auto pivot = [&](int k) {
     const double d = S[k * LD + k];
@@ -59,30 +59,34 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
     rdiag[k] = rl;
   };
   const int warp = t >> 5, lane = t & 31;
-  if (t == 0) pivot(0);
+  if (warp == 0) {
+    if (lane == 0) pivot(0);
+    __syncwarp();
+    const double rl = rdiag[0];
+    for (int i = 1 + lane; i < nb; i += 32) S[i] *= rl;
+    if (lane == 0) T[0] *= rl;
+  }
   __syncthreads();
   const int u = t - 32, ux = u & 15, uy = u >> 4;  // warps 1..7: a 16 x 14 grid
   for (int k = 0; k < nb; ++k) {
-    const double rl = rdiag[k];
-    if (warp == 0) {
-      for (int i = k + 1 + lane; i < nb; i += 32) S[k * LD + i] *= rl;
-    } else if (warp == 1) {
-      for (int j = lane; j <= k; j += 32) T[j * LD + k] *= rl;
-    }
-    __syncthreads();
     if (warp == 0) {
       if (k + 1 < nb) {
         const double lk1 = S[k * LD + k + 1];
         for (int i = k + 1 + lane; i < nb; i += 32)
           S[(k + 1) * LD + i] = fma(-S[k * LD + i], lk1, S[(k + 1) * LD + i]);
+        for (int j = lane; j <= k; j += 32) T[j * LD + k + 1] = fma(-lk1, T[j * LD + k], T[j * LD + k + 1]);
         __syncwarp();
         if (lane == 0) pivot(k + 1);
+        __syncwarp();
+        const double rl = rdiag[k + 1];
+        for (int i = k + 2 + lane; i < nb; i += 32) S[(k + 1) * LD + i] *= rl;
+        for (int j = lane; j <= k + 1; j += 32) T[j * LD + k + 1] *= rl;
       }
     } else {
       for (int j = k + 2 + ux; j < nb; j += 16)
         for (int i = j + uy; i < nb; i += 14) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
       for (int j = ux; j <= k; j += 16)
-        for (int i = k + 1 + uy; i < nb; i += 14) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+        for (int i = k + 2 + uy; i < nb; i += 14) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
     }
     __syncthreads();
   }
