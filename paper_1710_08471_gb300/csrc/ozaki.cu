@@ -729,7 +729,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
             }
             if (!ok) break;
             mma_commit(&aempty[slot]);
-            if (last) mma_commit(&accfull[ab * S + s]);  // every product of group s is issued
+            // every product of group s is issued; the Q-form's epilogue waits on groups 3 and S-1 only
+            if (last && (MODE == OZ_GRAM || CPT != 8 || s == 3 || s == S - 1)) mma_commit(&accfull[ab * S + s]);
             if (++slot == NA) {
               slot = 0;
               aph ^= 1u;
