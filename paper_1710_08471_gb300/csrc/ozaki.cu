@@ -714,8 +714,12 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
               const int nt = (S - s - t0 + (nm - q) - 1) / (nm - q);
               if (s == 0 && wait_acc) {  // first write of groups t0 .. t0+nt-1 in this buffer
 #pragma unroll
-                for (int g = t0; g < t0 + nt; ++g)
-                  if (!(ok = mbar_wait(&accempty[ab * S + g], (uint32_t)((use - 1) & 1), p.st))) break;
+                for (int g = t0; g < t0 + nt; ++g) {
+                  // the Q-form's epilogue releases each half (groups 0-3, 4-S-1) on its last barrier
+                  const bool rep = !(MODE == OZ_QFORM && CPT == 8) || g == 3 || g == S - 1 || g == t0 + nt - 1;
+                  const int gb = (MODE == OZ_QFORM && CPT == 8) ? (g <= 3 ? 3 : S - 1) : g;
+                  if (rep && !(ok = mbar_wait(&accempty[ab * S + gb], (uint32_t)((use - 1) & 1), p.st))) break;
+                }
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
               }
@@ -798,7 +802,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
         if (MODE == OZ_QFORM && CPT == 8) {
           // two waits per chunk: groups 0-3 are complete once slice 3's
           // commit has arrived (a commit tracks every earlier MMA), the rest
-          // once the last slice's has; all loads of a half share one wait
+          // once the last slice's has; all loads of a half share one wait,
+          // and each half is released on its last group's barrier (fewer
+          // barrier operations per tile: the Q-form is bound by its tile
+          // pipeline's hand-offs)
 #define OZ_HALF(G0, G1)                                                      \
   if (ok) {                                                                  \
     ok = mbar_wait(&accfull[ab * S + (G1)], par, p.st);                      \
@@ -810,7 +817,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       asm volatile("tcgen05.fence::before_thread_sync;");                    \
       __syncwarp();                                                          \
       if (lane == 0)                                                         \
-        _Pragma("unroll") for (int g = G0; g <= G1; ++g) mbar_arrive(&accempty[ab * S + g]); \
+        mbar_arrive(&accempty[ab * S + (G1)]);                               \
       if (G0 <= 0 && 0 <= G1) oz_accumulate<0, 8>(v[0 - G0], X, Y);         \
       if (G0 <= 1 && 1 <= G1) oz_accumulate<1, 8>(v[1 - G0], X, Y);         \
       if (G0 <= 2 && 2 <= G1) oz_accumulate<2, 8>(v[2 - G0], X, Y);         \
