@@ -64,10 +64,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@7f16f198549a7344": 2938854912,
-    "k_ozaki_gemm<7,QFORM>@tall@7f16f198549a7344": 23510839296,
-    "k_ozaki_gemm<7,GRAM>@mid@7f16f198549a7344": 1892679424,
-    "k_ozaki_gemm<7,GRAM>@tall@7f16f198549a7344": 15141435392,
+    "k_ozaki_gemm<7,QFORM>@mid@aba929302c1f63ed": 2939379712,
+    "k_ozaki_gemm<7,QFORM>@tall@aba929302c1f63ed": 23515037696,
+    "k_ozaki_gemm<7,GRAM>@mid@aba929302c1f63ed": 1892699136,
+    "k_ozaki_gemm<7,GRAM>@tall@aba929302c1f63ed": 15141593088,
     "k_cqr2_small_batched@batch@c56aa36f0d944e5a": 5306968320,
 }
 
