@@ -715,9 +715,9 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
               if (s == 0 && wait_acc) {  // first write of groups t0 .. t0+nt-1 in this buffer
 #pragma unroll
                 for (int g = t0; g < t0 + nt; ++g) {
-                  // the Q-form's epilogue releases each half (groups 0-3, 4-S-1) on its last barrier
-                  const bool rep = !(MODE == OZ_QFORM && CPT == 8) || g == 3 || g == S - 1 || g == t0 + nt - 1;
-                  const int gb = (MODE == OZ_QFORM && CPT == 8) ? (g <= 3 ? 3 : S - 1) : g;
+                  // the epilogue releases each half (groups 0-3, 4..S-1) on its last group's barrier
+                  const bool rep = g == 3 || g == S - 1 || g == t0 + nt - 1;
+                  const int gb = g <= 3 ? 3 : S - 1;
                   if (rep && !(ok = mbar_wait(&accempty[ab * S + gb], (uint32_t)((use - 1) & 1), p.st))) break;
                 }
                 if (!ok) break;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, EPI, NGRP>::THREADS, 1)
       oz_drain_group<G, CPT>(ta + G * BN, X, Y);                           \
       asm volatile("tcgen05.fence::before_thread_sync;");                  \
       __syncwarp();                                                        \
-      if (lane == 0) mbar_arrive(&accempty[ab * S + G]);                   \
+      if (lane == 0 && (G == 3 || G == S - 1)) mbar_arrive(&accempty[ab * S + G]); \
     }                                                                      \
   }
         if (MODE == OZ_QFORM && CPT == 8) {
