@@ -46,7 +46,10 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   //     k+1 (its square root and reciprocal from a short Newton sequence) and
   //     scales that column and row by 1/l_(k+1,k+1);
   //   - the other warps apply step k to the rest of the trailing matrix and to
-  //     the rows of Y below k+1;
+  //     the rows of Y below k+1, numbered consecutively (the triangle's part
+  //     through a table of its elements, column by column) so that nearly
+  //     every FP64 warp instruction updates 32 of them -- the FP64 pipe
+  //     charges an instruction in full whatever its active lanes;
   // with one block barrier per step. Every element sees the same operations in
   // the same order as the plain factorization followed by the plain inverse.
   __shared__ double rdiag[NB];
@@ -67,7 +70,16 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
     if (lane == 0) T[0] *= rl;
   }
   __syncthreads();
-  const int u = t - 32, ux = u & 15, uy = u >> 4;  // warps 1..7: a 16 x 14 grid
+  const int u = t - 32;  // warps 1..7 share the packed trailing elements
+  // the lower triangle column by column, (j << 8) | i: the trailing part of
+  // step k is the suffix from column k+2 on
+  __shared__ unsigned short tab[NB * (NB + 1) / 2];
+  if (t < nb) {
+    const int st = t * nb - t * (t - 1) / 2;
+    for (int i = t; i < nb; ++i) tab[st + i - t] = (unsigned short)((t << 8) | i);
+  }
+  __syncthreads();
+  const int ntri = nb * (nb + 1) / 2;
   for (int k = 0; k < nb; ++k) {
     if (warp == 0) {
       if (k + 1 < nb) {
@@ -83,10 +95,20 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
         for (int j = lane; j <= k + 1; j += 32) T[j * LD + k + 1] *= rl;
       }
     } else {
-      for (int j = k + 2 + ux; j < nb; j += 16)
-        for (int i = j + uy; i < nb; i += 14) S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
-      for (int j = ux; j <= k; j += 16)
-        for (int i = k + 2 + uy; i < nb; i += 14) T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+      const int s0 = (k + 2) * nb - (k + 2) * (k + 1) / 2;  // start of column k+2
+      const int cS = k + 2 < nb ? ntri - s0 : 0;
+      const int h = nb - k - 2;
+      const int cT = h > 0 ? (k + 1) * h : 0;
+      const float rh = h > 0 ? 1.0f / (float)h : 0.0f;
+      for (int e = u; e < cS + cT; e += 224) {
+        if (e < cS) {
+          const int ji = tab[s0 + e], j = ji >> 8, i = ji & 255;
+          S[j * LD + i] = fma(-S[k * LD + i], S[k * LD + j], S[j * LD + i]);
+        } else {
+          const int e2 = e - cS, j = __float2int_rz(((float)e2 + 0.5f) * rh), i = k + 2 + (e2 - j * h);
+          T[j * LD + i] = fma(-S[k * LD + i], T[j * LD + k], T[j * LD + i]);
+        }
+      }
     }
     __syncthreads();
   }
