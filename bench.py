@@ -64,10 +64,10 @@ GB300_SMS = 152
 NCU_TRAFFIC = {
     "k_qform_gram_small@mid@32201450a5426255": 2145473280,
     "k_qform_gram_small@tall@32201450a5426255": 17163786240,
-    "k_ozaki_gemm<7,QFORM>@mid@aba929302c1f63ed": 2939379712,
-    "k_ozaki_gemm<7,QFORM>@tall@aba929302c1f63ed": 23515037696,
-    "k_ozaki_gemm<7,GRAM>@mid@aba929302c1f63ed": 1892699136,
-    "k_ozaki_gemm<7,GRAM>@tall@aba929302c1f63ed": 15141593088,
+    "k_ozaki_gemm<7,QFORM>@mid@f33dc9b14d75de37": 2938640128,
+    "k_ozaki_gemm<7,QFORM>@tall@f33dc9b14d75de37": 23509121024,
+    "k_ozaki_gemm<7,GRAM>@mid@f33dc9b14d75de37": 1892780800,
+    "k_ozaki_gemm<7,GRAM>@tall@f33dc9b14d75de37": 15142246400,
     "k_cqr2_small_batched@batch@c56aa36f0d944e5a": 5306968320,
 }
 
@@ -230,7 +230,14 @@ def workload_config(args, ws: int) -> dict:
     return {"workload": desc, "m": m, "n": n, "kappa": kappa, "precision": args.precision,
             "variant": "fused" if fused else "plain", "inverse_depth": args.inverse_depth, "graph": args.graph,
             "parallelism": f"replicas{ws}" if ws > 1 else "single",
-            "l2": f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)"}
+            "l2": ("512 MB buffer rewritten between steps (outside the timed events)" if needs_flush(m, n)
+                   else f"inputs {m * n * 8 / 1e9:.1f} GB > 129 MB L2 (no flush)")}
+
+
+def needs_flush(m: int, n: int) -> bool:
+    """An input that fits in L2 (129 MB) would stay there from one step to
+    the next: such workloads rewrite a 512 MB buffer between timed steps."""
+    return m * n * 8 <= 129 * 2**20
 
 
 def bench_reference(args, ws, rank):
@@ -774,8 +781,10 @@ def bench_ours(args, ws, rank, local):
             pl.set_inverse_depth(depth)
         return pl
 
+    flush = torch.zeros(64 << 20, dtype=torch.float64, device=dev) if needs_flush(m, n) else None
+
     def timed(pl, steps, warmup, profile):
-        return timed_plan(pl, A, Q, R, stream, steps, warmup, profile, ws)
+        return timed_plan(pl, A, Q, R, stream, steps, warmup, profile, ws, flush=flush)
 
     plan = make_plan(args.precision, fused, args.inverse_depth, graph=args.graph)
     clocks = ClockSampler(local)

@@ -1,7 +1,7 @@
 // Reads "mode bits pert" lines from stdin (bits: an FP64 bit pattern as a
 // signed decimal; pert: a seed perturbation in float ulps) and prints hex bit
 // patterns of the pivot routine's results.
-// mode 0: chol_rsqrt(d) -> "r l"; mode 1: rs_newton2(f, seed perturbed by
+// mode 0: chol_rsqrt(d) -> "r l"; mode 1: rs_refine3(f, seed perturbed by
 // pert float ulps) for f = d in [1, 4) -> "y".
 #include <cstdio>
 #include <cstring>
@@ -30,7 +30,7 @@ int main() {
       memcpy(&u, &s, sizeof u);
       u += (unsigned)pert;
       memcpy(&s, &u, sizeof s);
-      std::printf("%016llx\n", bits_of(cqr2::rs_newton2(d, (double)s)));
+      std::printf("%016llx\n", bits_of(cqr2::rs_refine3(d, (double)s)));
     }
   }
   return 0;
