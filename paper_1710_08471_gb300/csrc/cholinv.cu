@@ -121,15 +121,13 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
   }
 }
 
-// The 64 x 64 base case (every leaf of a recursion on n = 64 2^p), with its
-// steps compiled one by one. FP64 on GB300 issues under three rules that
-// decide this design: a dependent FP64 operation takes 64 clocks; the SM
-// starts at most one FP64 warp instruction per 16 clocks; and an instruction
-// whose lanes are all predicated off still takes its slot. The runtime kernel
-// above spends about 25 instructions of index arithmetic and shared-memory
-// traffic on each trailing update, as a dependency chain per warp. Here, with
-// the step k a compile-time constant, every count and bound below is a
-// constant and no inactive slot is issued:
+// The 64 x 64 base case (every leaf of a recursion on n = 64 2^p). FP64 on
+// GB300 issues under three rules that decide this design: a dependent FP64
+// operation takes 64 clocks; the SM starts at most one FP64 warp instruction
+// per 16 clocks; and an instruction whose lanes are all predicated off still
+// takes its slot. The runtime kernel above spends about 25 instructions of
+// index arithmetic and shared-memory traffic on each trailing update, as a
+// dependency chain per warp. Here:
 //  - warp 0 applies step k to column k+1 of L (from the diagonal down) and to
 //    row k+1 of Y = L^-1 (left of the diagonal), 64 elements in two warp
 //    instructions, forms the pivot from lane 0's element and scales both; the
@@ -137,147 +135,42 @@ __global__ void __launch_bounds__(256) k_cholinv_base(const double* __restrict__
 //  - five bulk warps keep the trailing part of L in registers: element
 //    (i, j), 2 <= j <= i < 64, at position e' = u + 160 s of the column-major
 //    packed order read backwards, so that the elements still active at step
-//    k (j >= k + 2) are the first (62 - k)(63 - k)/2 positions; each step
-//    they write out column k+2, which warp 0 takes over next;
+//    k (j >= k + 2) fill the first slots; a fall-through switch on the count
+//    of active slots issues exactly those; each step they write out column
+//    k+2, which warp 0 takes over next;
 //  - the bulk warps update Y's trailing block (rows k+2.., columns 0..k) in
-//    shared memory, numbered column by column (constant divisors), with all
-//    loads ahead of the FMAs and the stores behind them.
+//    shared memory, numbered column by column (division by a multiply-shift
+//    from a table), two elements per pass with both loads ahead of the FMAs.
+// The step loop stays a loop: compiled step by step the kernel ran 8% faster
+// while its code was hot but was 16 times larger (410 KB) and, after large
+// kernels had refilled L2, took 1.6 times as long.
 // Every element sees the same operations in the same order as in the runtime
 // kernel, so the two agree bit for bit.
-namespace base64 {
+constexpr int B64_BW = 5;                       // bulk warps
+constexpr int B64_P = 32 * B64_BW;              // bulk threads
+constexpr int B64_NL = (NB - 2) * (NB - 1) / 2;  // trailing elements of L
+constexpr int B64_NS = (B64_NL + B64_P - 1) / B64_P;  // register slots per bulk thread
+static_assert(B64_NS <= 16, "the slot switch has 16 cases");
 
-constexpr int BW = 5;                    // bulk warps
-constexpr int P = 32 * BW;               // bulk threads
-constexpr int NL = (NB - 2) * (NB - 1) / 2;  // trailing elements of L
-constexpr int NS = (NL + P - 1) / P;     // register slots per bulk thread
-
-struct Ctx {
-  double* S;
-  double* T;
-  double z[NS];
-  int row[NS], col[NS];
-  int u;
-};
-
-template <int K>
-__device__ __forceinline__ void bulk(Ctx& c) {
-  constexpr int cS = (62 - K) * (63 - K) / 2;                // active L positions
-  constexpr int cS1 = K <= 61 ? (61 - K) * (62 - K) / 2 : 0;  // still active next step
-  constexpr int h = 62 - K;                                  // rows of Y's block
-  constexpr int cY = h > 0 ? h * (K + 1) : 0;
-  constexpr int NY = (cY + P - 1) / P;
-  constexpr int NA = (cS + P - 1) / P;
-  constexpr int NYA = NY > 0 ? NY : 1;
-  double* S = c.S;
-  double* T = c.T;
-  const double* Sk = S + K * LD;
-  double yx[NYA], yy[NYA], yz[NYA];
-  int yd[NYA];
-#pragma unroll
-  for (int s = 0; s < NY; ++s) {
-    const int e = c.u + P * s;
-    const int j = e / (h > 0 ? h : 1), i = K + 2 + (e - j * h);
-    const bool in = (s + 1) * P <= cY || e < cY;
-    yd[s] = in ? j * LD + i : -1;
-    if (in) {
-      yx[s] = Sk[i];
-      yy[s] = T[j * LD + K];
-      yz[s] = T[j * LD + i];
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < NA; ++s) {
-    const double r = fma(-Sk[c.row[s]], Sk[c.col[s]], c.z[s]);
-    if ((s + 1) * P <= cS)
-      c.z[s] = r;
-    else
-      c.z[s] = (c.u + P * s < cS) ? r : c.z[s];
-  }
-#pragma unroll
-  for (int s = 0; s < NY; ++s)
-    if (yd[s] >= 0) yz[s] = fma(-yx[s], yy[s], yz[s]);
-#pragma unroll
-  for (int s = 0; s < NY; ++s)
-    if (yd[s] >= 0) T[yd[s]] = yz[s];
-  if constexpr (cS > 0) {
-    // column K+2: positions cS1 .. cS-1
-#pragma unroll
-    for (int s = cS1 / P; s < NA; ++s) {
-      const int ep = c.u + P * s;
-      if (ep >= cS1 && ep < cS) S[(K + 2) * LD + c.row[s]] = c.z[s];
-    }
-  }
-}
-
-template <int K>
-__device__ __forceinline__ void pivot_warp(double* S, double* T, int lane, DevStatus* st, int pass, long long off) {
-  constexpr int k1 = K + 1, ns = NB - k1;
-  double* smem = S;
-  const double lk1 = S[K * LD + k1];
-  int od[2];
-  double v[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int e = lane + 32 * q;
-    int ox = 0;
-    od[q] = -1;
-    if (e < ns) {
-      od[q] = k1 * LD + k1 + e;
-      ox = K * LD + k1 + e;
-    } else if (e < NB) {
-      od[q] = NB * LD + (e - ns) * LD + k1;
-      ox = NB * LD + (e - ns) * LD + K;
-    }
-    v[q] = od[q] >= 0 ? fma(-smem[ox], lk1, smem[od[q]]) : 0.0;
-  }
-  double rl = 0.0, l = 0.0;
-  bool fast = true;
-  if (lane == 0) {
-    const double d = v[0];
-    // d <= 0, NaN or infinite, tested on the bits (no FP64 compare on the chain)
-    const unsigned long long db = (unsigned long long)__double_as_longlong(d);
-    if ((db >> 63) != 0 || db == 0 || ((db >> 52) & 0x7FF) == 0x7FF) report_pivot(st, pass, off + k1, d);
-    fast = chol_rsqrt_r(d, &rl, &l);
-    T[k1 * LD + k1] = rl;  // Y's diagonal: 1 / l
-  }
-  rl = __shfl_sync(0xffffffffu, rl, 0);
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-    if (od[q] >= 0) smem[od[q]] = v[q] * rl;  // lane 0: the diagonal d / sqrt(d)
-  if (!fast) S[k1 * LD + k1] = l;
-}
-
-template <int K>
-__device__ __forceinline__ void steps(Ctx& c, int warp, int lane, DevStatus* st, int pass, long long off) {
-  if (warp == 0) {
-    if constexpr (K + 1 < NB) pivot_warp<K>(c.S, c.T, lane, st, pass, off);
-  } else {
-    bulk<K>(c);
-  }
-  __syncthreads();
-  if constexpr (K + 2 < NB) steps<K + 1>(c, warp, lane, st, pass, off);
-}
-
-}  // namespace base64
-
-__global__ void __launch_bounds__(32 * (base64::BW + 1), 1)
+__global__ void __launch_bounds__(32 * (B64_BW + 1), 1)
     k_cholinv_base64(const double* __restrict__ Wk, int64_t ldk, double* __restrict__ L, int64_t ldl,
                      double* __restrict__ Y, int64_t ldy, DevStatus* st, int pass, long long off) {
-  using namespace base64;
-  constexpr int NT = 32 * (BW + 1);
+  constexpr int NT = 32 * (B64_BW + 1), P = B64_P, NS = B64_NS;
   extern __shared__ double smem[];
-  Ctx c;
-  c.S = smem;            // S(i, j) = S[j * LD + i], lower part
-  c.T = smem + NB * LD;  // Y
-  double* S = c.S;
-  double* T = c.T;
+  double* S = smem;            // S(i, j) = S[j * LD + i], lower part
+  double* T = smem + NB * LD;  // Y
+  __shared__ unsigned mdiv[NB];  // floor(e / h) = (e * mdiv[h]) >> 16 for e < 1024, h < 64
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int e = t; e < NB * NB; e += NT) {
     const int i = e % NB, j = e / NB;
     S[j * LD + i] = (i >= j) ? Wk[i + (int64_t)j * ldk] : 0.0;
     T[j * LD + i] = (i == j) ? 1.0 : 0.0;
   }
+  if (t < NB) mdiv[t] = t > 0 ? (1u << 16) / (unsigned)t + 1 : 0;
   __syncthreads();
+  double z[NS];
+  int row[NS], col[NS], cmax[NS];  // cmax: the slot's largest column (lane 0's)
+  const int u = t - 32;
   if (warp == 0) {
     double rl = 0.0, l = 0.0;
     if (lane == 0) {
@@ -290,13 +183,12 @@ __global__ void __launch_bounds__(32 * (base64::BW + 1), 1)
     rl = __shfl_sync(0xffffffffu, rl, 0);
     for (int i = 1 + lane; i < NB; i += 32) S[i] *= rl;
   } else {
-    c.u = t - 32;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const int ep = c.u + P * s;
+      const int ep = u + P * s;
       int i = 0, j = 0;
-      if (ep < NL) {
-        int p = NL - 1 - ep;  // position in the forward column-major order of columns 2..
+      if (ep < B64_NL) {
+        int p = B64_NL - 1 - ep;  // position in the forward column-major order of columns 2..
         j = 2;
         while (p >= NB - j) {
           p -= NB - j;
@@ -304,13 +196,93 @@ __global__ void __launch_bounds__(32 * (base64::BW + 1), 1)
         }
         i = j + p;
       }
-      c.row[s] = i;
-      c.col[s] = j;
-      c.z[s] = (j >= 2) ? S[j * LD + i] : 0.0;
+      row[s] = i;
+      col[s] = j;
+      z[s] = (j >= 2) ? S[j * LD + i] : 0.0;
+      cmax[s] = __shfl_sync(0xffffffffu, j, 0);
     }
   }
   __syncthreads();
-  steps<0>(c, warp, lane, st, pass, off);
+  for (int k = 0; k < NB - 1; ++k) {
+    const int k1 = k + 1, kb = k * LD;
+    if (warp == 0) {
+      const int ns = NB - k1;
+      const double lk1 = S[kb + k1];
+      int od[2];
+      double v[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int e = lane + 32 * q;
+        int ox = 0;
+        od[q] = -1;
+        if (e < ns) {
+          od[q] = k1 * LD + k1 + e;
+          ox = kb + k1 + e;
+        } else if (e < NB) {
+          od[q] = NB * LD + (e - ns) * LD + k1;
+          ox = NB * LD + (e - ns) * LD + k;
+        }
+        v[q] = od[q] >= 0 ? fma(-smem[ox], lk1, smem[od[q]]) : 0.0;
+      }
+      double rl = 0.0, l = 0.0;
+      bool fast = true;
+      if (lane == 0) {
+        const double d = v[0];
+        // d <= 0, NaN or infinite, tested on the bits (no FP64 compare on the chain)
+        const unsigned long long db = (unsigned long long)__double_as_longlong(d);
+        if ((db >> 63) != 0 || db == 0 || ((db >> 52) & 0x7FF) == 0x7FF) report_pivot(st, pass, off + k1, d);
+        fast = chol_rsqrt_r(d, &rl, &l);
+        T[k1 * LD + k1] = rl;  // Y's diagonal: 1 / l
+      }
+      rl = __shfl_sync(0xffffffffu, rl, 0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (od[q] >= 0) smem[od[q]] = v[q] * rl;  // lane 0: the diagonal d / sqrt(d)
+      if (!fast) S[k1 * LD + k1] = l;
+    } else {
+      int na = NS;  // slots with an active lane: a prefix
+#pragma unroll
+      for (int s = NS - 1; s >= 0; --s)
+        if (cmax[s] < k + 2) na = s;
+#define CQ2_SLOT(s)                                                   \
+  case (s) + 1:                                                       \
+    if constexpr ((s) < NS) {                                         \
+      const double r = fma(-S[kb + row[s]], S[kb + col[s]], z[s]);    \
+      z[s] = col[s] >= k + 2 ? r : z[s];                              \
+    }
+      switch (na) {
+        CQ2_SLOT(15) CQ2_SLOT(14) CQ2_SLOT(13) CQ2_SLOT(12) CQ2_SLOT(11) CQ2_SLOT(10) CQ2_SLOT(9) CQ2_SLOT(8)
+        CQ2_SLOT(7) CQ2_SLOT(6) CQ2_SLOT(5) CQ2_SLOT(4) CQ2_SLOT(3) CQ2_SLOT(2) CQ2_SLOT(1) CQ2_SLOT(0)
+        default:
+          break;
+      }
+#undef CQ2_SLOT
+      // Y rows k+2.., columns 0..k, numbered column by column, two per pass
+      const int h = NB - 2 - k, cY = h > 0 ? h * k1 : 0;
+      const unsigned m = mdiv[h > 0 ? h : 1];
+      for (int e0 = u; e0 < cY; e0 += 2 * P) {
+        const int e1 = e0 + P;
+        const bool in1 = e1 < cY;
+        const int j0 = (int)(((unsigned)e0 * m) >> 16), i0 = k + 2 + (e0 - j0 * h);
+        const int j1 = (int)(((unsigned)e1 * m) >> 16), i1 = k + 2 + (e1 - j1 * h);
+        const double x0 = S[kb + i0], y0 = T[j0 * LD + k], z0 = T[j0 * LD + i0];
+        double x1 = 0.0, y1 = 0.0, z1 = 0.0;
+        if (in1) {
+          x1 = S[kb + i1];
+          y1 = T[j1 * LD + k];
+          z1 = T[j1 * LD + i1];
+        }
+        const double r0 = fma(-x0, y0, z0);
+        const double r1 = fma(-x1, y1, z1);
+        T[j0 * LD + i0] = r0;
+        if (in1) T[j1 * LD + i1] = r1;
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (col[s] == k + 2) S[(k + 2) * LD + row[s]] = z[s];
+    }
+    __syncthreads();
+  }
   for (int e = t; e < NB * NB; e += NT) {
     const int i = e % NB, j = e / NB;
     if (i >= j) {
@@ -352,7 +324,7 @@ cudaError_t set_base_smem() {
 cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
                 int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s, double* ws, size_t wsn) {
   if (n == NB) {
-    k_cholinv_base64<<<1, 32 * (base64::BW + 1), BASE_SMEM, s>>>(Wk, ldk, L, ldl, Y, ldy, st, pass, off);
+    k_cholinv_base64<<<1, 32 * (B64_BW + 1), BASE_SMEM, s>>>(Wk, ldk, L, ldl, Y, ldy, st, pass, off);
     count_launch();
     return cudaGetLastError();
   }
