@@ -118,6 +118,17 @@ constexpr int GRAM_CPS_MAX = 8;
     if (e_ != cudaSuccess) return CQR2_ERR_CUDA; \
   } while (0)
 
+// R = op(A) B of two upper-triangular factors (R = R2 R1 of Algorithm CQR2,
+// R = R' R0 of the shifted variant); op(A) = A^T when A holds a lower
+// Cholesky factor.
+cudaError_t r_product(cqr2_plan_st* p, int n, const double* A, int64_t lda, bool a_trans, const double* B,
+                      int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+  if (n <= TRMM_SMALL_MAX) return trmm_upper_small(n, A, lda, a_trans, B, ldb, C, ldc, s);
+  return gemm_f64(n, n, n, 1.0, A, lda, B, ldb, 0.0, C, ldc,
+                  (a_trans ? GEMM_TA : 0u) | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws,
+                  cholinv_splitk_doubles());
+}
+
 // Copy a column-major rows x cols block: one linear copy when both sides are
 // packed (ld == rows), which runs at full link bandwidth, else a pitched copy.
 cudaError_t copy_cols(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t rows, int64_t cols,
@@ -318,9 +329,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
   }
   {
     Stage st(p, CQR2_STAGE_TRMM);
-    TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
-                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws,
-                 cholinv_splitk_doubles()));
+    TRY(r_product(p, n, p->L, n, true, p->R1, n, dR, ldr, s));
   }
   return CQR2_OK;
 }
@@ -420,9 +429,7 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   // ---- R = R2 R1 with R2 = L2^T
   {
     Stage st(p, CQR2_STAGE_TRMM);
-    TRY(gemm_f64(n, n, n, 1.0, p->L, n, p->R1, n, 0.0, dR, ldr,
-                 GEMM_TA | GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws,
-                 cholinv_splitk_doubles()));
+    TRY(r_product(p, n, p->L, n, true, p->R1, n, dR, ldr, s));
   }
   return CQR2_OK;
 }
@@ -521,8 +528,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   cqr2_status_t r = factor_impl(p, dQ, ldq, dQ, ldq, p->Rt, n, 1);
   if (r != CQR2_OK) return r;
   Stage st(p, CQR2_STAGE_TRMM);
-  TRY(gemm_f64(n, n, n, 1.0, p->Rt, n, p->R0, n, 0.0, dR, ldr,
-               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, s, p->skws, cholinv_splitk_doubles()));
+  TRY(r_product(p, n, p->Rt, n, false, p->R0, n, dR, ldr, s));
   return CQR2_OK;
 }
 
@@ -1001,9 +1007,7 @@ cqr2_status_t cqr2_trmm_upper(cqr2_plan_t p, const double* dR2, int64_t ld2, con
   cqr2_status_t r = check_device(p);
   if (r != CQR2_OK) return r;
   const int n = (int)p->n;
-  TRY(gemm_f64(n, n, n, 1.0, dR2, ld2, dR1, ld1, 0.0, dR, ldr,
-               GEMM_A_UPPER | GEMM_B_UPPER | GEMM_C_UPPER | GEMM_BETA0, p->stream, p->skws,
-               cholinv_splitk_doubles()));
+  TRY(r_product(p, n, dR2, ld2, false, dR1, ld1, dR, ldr, p->stream));
   return CQR2_OK;
 }
 

@@ -212,4 +212,38 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
   return cudaGetLastError();
 }
 
+// R = op(A) B of two upper-triangular n x n factors (the R2 R1 of Algorithm
+// CQR2), n <= TRMM_SMALL_MAX, in one launch: CTA j forms column j and thread
+// i sums op(A)(i, k) B(k, j) for k = i..j in order; C below the diagonal is
+// written as 0. op(A)(i, k) = A(k, i) when a_trans (A holds the lower
+// transpose, as the Cholesky factor L2 does), else A(i, k). The general GEMM
+// needs a split-k launch and its reduction for this 2 n^3 / 6 flop product.
+__global__ void __launch_bounds__(TRMM_SMALL_MAX) k_trmm_upper_small(int n, const double* __restrict__ A, int64_t lda,
+                                                                     bool a_trans, const double* __restrict__ B,
+                                                                     int64_t ldb, double* __restrict__ C, int64_t ldc) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  if (i <= j) {
+    const double* b = B + (int64_t)j * ldb;
+    if (a_trans) {
+      const double* a = A + (int64_t)i * lda;  // column i of the lower factor
+#pragma unroll 4
+      for (int k = i; k <= j; ++k) acc = fma(a[k], b[k], acc);
+    } else {
+#pragma unroll 4
+      for (int k = i; k <= j; ++k) acc = fma(A[i + (int64_t)k * lda], b[k], acc);
+    }
+  }
+  C[i + (int64_t)j * ldc] = acc;
+}
+
+cudaError_t trmm_upper_small(int n, const double* A, int64_t lda, bool a_trans, const double* B, int64_t ldb,
+                             double* C, int64_t ldc, cudaStream_t s) {
+  if (n < 1 || n > TRMM_SMALL_MAX) return cudaErrorInvalidValue;
+  k_trmm_upper_small<<<n, (n + 31) / 32 * 32, 0, s>>>(n, A, lda, a_trans, B, ldb, C, ldc);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace cqr2

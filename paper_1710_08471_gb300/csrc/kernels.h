@@ -74,6 +74,12 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
                      const double* B, int64_t ldb, double beta, double* C, int64_t ldc, unsigned flags,
                      cudaStream_t s, double* ws = nullptr, size_t ws_doubles = 0);
 
+// R = op(A) B for upper-triangular n x n factors, n <= TRMM_SMALL_MAX, one
+// launch; op(A) = A^T (A lower) when a_trans. C below the diagonal is zeroed.
+constexpr int TRMM_SMALL_MAX = 128;
+cudaError_t trmm_upper_small(int n, const double* A, int64_t lda, bool a_trans, const double* B, int64_t ldb,
+                             double* C, int64_t ldc, cudaStream_t s);
+
 // ---------------------------------------------------------------- CholInv
 // [L, Y] = CholInv(W) (Algorithm 1): recursive halving with FP64 GEMMs and a
 // one-CTA base case of size <= 64. `work` and `U` are n x n scratch (ld n).

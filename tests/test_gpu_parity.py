@@ -125,7 +125,7 @@ def test_qform(cq, m, n, kappa):
     assert np.all(np.abs(Q - Qo) <= bound + 1e-300)
 
 
-@pytest.mark.parametrize("n", [1, 5, 64, 130, 300])
+@pytest.mark.parametrize("n", [1, 5, 64, 127, 128, 129, 300])
 def test_trmm_upper(cq, n):
     rng = np.random.default_rng(n)
     R2 = np.triu(rng.standard_normal((n, n))) + np.tril(np.ones((n, n)), -1) * 3.0  # garbage below
