@@ -191,12 +191,19 @@ cudaError_t hx_wait_input(cqr2_plan_st* p, cudaStream_t s) {
 }
 
 // [L, Y] = CholInv(W) of the plan's pass, with the plan's inverse depth.
-cudaError_t plan_cholinv(cqr2_plan_st* p, int pass, cudaStream_t s) {
+// [L, Y] = CholInv(W) into the plan's L and Y, and, when given, R = L^T into Rt
+// (ld n) and the Q-form's packed R^-1 into Rp.
+cudaError_t plan_cholinv(cqr2_plan_st* p, int pass, cudaStream_t s, double* Rt = nullptr, double* Rp = nullptr) {
   const int n = (int)p->n;
-  if (p->inv_depth > 0)
-    return cholinv_depth(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->Tsolve, p->ldt, p->st, pass, p->inv_depth,
-                         s, p->skws, cholinv_splitk_doubles());
-  return cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s, p->skws, cholinv_splitk_doubles());
+  if (p->inv_depth > 0) {
+    cudaError_t e = cholinv_depth(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->Tsolve, p->ldt, p->st, pass,
+                                  p->inv_depth, s, p->skws, cholinv_splitk_doubles());
+    if (e == cudaSuccess && Rt != nullptr) e = transpose_lower(p->L, n, n, Rt, n, s);
+    if (e == cudaSuccess && Rp != nullptr) e = pack_rinv_from_lower(p->Y, n, n, Rp, s);
+    return e;
+  }
+  return cholinv(n, p->W, n, p->L, n, p->Y, n, p->Wk, p->U, p->st, pass, s, p->skws, cholinv_splitk_doubles(), Rt,
+                 n, Rp);
 }
 
 // X = B R^-1 = B L^-T (general path, rows x n): one triangular multiply by
@@ -308,8 +315,7 @@ cqr2_status_t factor_impl_ozaki(cqr2_plan_st* p, const double* dA, int64_t lda, 
     }
     {
       Stage st(p, pass == 1 ? CQR2_STAGE_CHOLINV1 : CQR2_STAGE_CHOLINV2);
-      TRY(plan_cholinv(p, pass_base + pass, s));
-      if (pass == 1) TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
+      TRY(plan_cholinv(p, pass_base + pass, s, pass == 1 ? p->R1 : nullptr));  // R1 = L1^T
     }
     {
       Stage st(p, CQR2_STAGE_SPLIT);
@@ -368,15 +374,14 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
-    TRY(plan_cholinv(p, pass_base + 1, s));
-    TRY(transpose_lower(p->L, n, n, p->R1, n, s));  // R1 = L1^T
+    // R1 = L1^T, and on the small path R1^-1 packed for the Q-form
+    TRY(plan_cholinv(p, pass_base + 1, s, p->R1, p->small ? p->Rp : nullptr));
   }
   // ---- Q1 = A R1^-1 (staged in dQ on the small path), then pass 2 on Q1
   const double* X2 = dQ;
   int64_t ldx2 = ldq;
   if (p->small) {
     Stage st(p, CQR2_STAGE_QFORM1);
-    TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
     if (p->fused) {
       // Q1 and the partial Grams of Q1 in one sweep over A
       TRY(qform_gram_small(dA, lda, p->cm, n, p->Rp, dQ, ldq, p->g, p->partial, s));
@@ -396,11 +401,10 @@ cqr2_status_t factor_impl(cqr2_plan_st* p, const double* dA, int64_t lda, double
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV2);
-    TRY(plan_cholinv(p, pass_base + 2, s));
+    TRY(plan_cholinv(p, pass_base + 2, s, nullptr, p->small ? p->Rp : nullptr));
   }
   {
     Stage st(p, CQR2_STAGE_QFORM2);
-    if (p->small) TRY(pack_rinv_from_lower(p->Y, n, n, p->Rp, s));
     // Host-buffer call: the last Q-form runs by row blocks, each copied out on
     // the copy stream while the next block is formed.
     const int nb = p->hx.on ? HX_BLOCKS : 1;
@@ -504,8 +508,7 @@ cqr2_status_t factor_any(cqr2_plan_st* p, const double* dA, int64_t lda, double*
   }
   {
     Stage st(p, CQR2_STAGE_CHOLINV1);
-    TRY(plan_cholinv(p, 1, s));
-    TRY(transpose_lower(p->L, n, n, p->R0, n, s));  // R0 = L0^T
+    TRY(plan_cholinv(p, 1, s, p->R0));  // R0 = L0^T
   }
   {
     Stage st(p, CQR2_STAGE_QFORM1);

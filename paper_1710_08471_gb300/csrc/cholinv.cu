@@ -152,9 +152,13 @@ constexpr int B64_NL = (NB - 2) * (NB - 1) / 2;  // trailing elements of L
 constexpr int B64_NS = (B64_NL + B64_P - 1) / B64_P;  // register slots per bulk thread
 static_assert(B64_NS <= 16, "the slot switch has 16 cases");
 
+// Writes the whole 64 x 64 blocks of L and Y (zeros above the diagonal) and,
+// when given, R = L^T (zeros below) and the Q-form's packed R^-1 (column
+// groups of rpw, see k_pack_rinv). W is read completely before anything is
+// written, so it may share storage with an output.
 __global__ void __launch_bounds__(32 * (B64_BW + 1), 1)
-    k_cholinv_base64(const double* __restrict__ Wk, int64_t ldk, double* __restrict__ L, int64_t ldl,
-                     double* __restrict__ Y, int64_t ldy, DevStatus* st, int pass, long long off) {
+    k_cholinv_base64(const double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* Rt,
+                     int64_t ldrt, double* Rp, int rpw, DevStatus* st, int pass, long long off) {
   constexpr int NT = 32 * (B64_BW + 1), P = B64_P, NS = B64_NS;
   extern __shared__ double smem[];
   double* S = smem;            // S(i, j) = S[j * LD + i], lower part
@@ -285,9 +289,15 @@ __global__ void __launch_bounds__(32 * (B64_BW + 1), 1)
   }
   for (int e = t; e < NB * NB; e += NT) {
     const int i = e % NB, j = e / NB;
-    if (i >= j) {
-      L[i + (int64_t)j * ldl] = S[j * LD + i];
-      Y[i + (int64_t)j * ldy] = T[j * LD + i];
+    L[i + (int64_t)j * ldl] = i >= j ? S[j * LD + i] : 0.0;
+    Y[i + (int64_t)j * ldy] = i >= j ? T[j * LD + i] : 0.0;
+    if (Rt != nullptr) Rt[i + (int64_t)j * ldrt] = i <= j ? S[i * LD + j] : 0.0;  // R(i, j) = L(j, i)
+  }
+  if (Rp != nullptr) {
+    // element e of the packing: group g, row k, column c within the group
+    for (int e = t; e < RP_GROUPS * NB * rpw; e += NT) {
+      const int c = e % rpw, k = (e / rpw) % NB, col = (e / (rpw * NB)) * rpw + c;
+      Rp[e] = (col < NB && k <= col) ? T[k * LD + col] : 0.0;  // R^-1(k, col) = Y(col, k)
     }
   }
 }
@@ -324,7 +334,8 @@ cudaError_t set_base_smem() {
 cudaError_t rec(int n, double* Wk, int64_t ldk, double* L, int64_t ldl, double* Y, int64_t ldy, double* U,
                 int64_t ldu, DevStatus* st, int pass, long long off, cudaStream_t s, double* ws, size_t wsn) {
   if (n == NB) {
-    k_cholinv_base64<<<1, 32 * (B64_BW + 1), BASE_SMEM, s>>>(Wk, ldk, L, ldl, Y, ldy, st, pass, off);
+    k_cholinv_base64<<<1, 32 * (B64_BW + 1), BASE_SMEM, s>>>(Wk, ldk, L, ldl, Y, ldy, nullptr, 0, nullptr, 0, st,
+                                                                 pass, off);
     count_launch();
     return cudaGetLastError();
   }
@@ -443,9 +454,17 @@ cudaError_t cholinv_depth(int n, const double* W, int64_t ldw, double* L, int64_
 }
 
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
-                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s, double* ws, size_t wsn) {
+                    double* work, double* U, DevStatus* st, int pass, cudaStream_t s, double* ws, size_t wsn,
+                    double* Rt, int64_t ldrt, double* Rp) {
   cudaError_t e;
   if ((e = set_base_smem()) != cudaSuccess) return e;
+  if (n == NB) {
+    // one base case: straight from W, with R and the packed R^-1 when asked
+    const int rpw = Rp != nullptr ? qform_group_width(n) : 0;
+    k_cholinv_base64<<<1, 32 * (B64_BW + 1), BASE_SMEM, s>>>(W, ldw, L, ldl, Y, ldy, Rt, ldrt, Rp, rpw, st, pass, 0);
+    count_launch();
+    return cudaGetLastError();
+  }
   if ((e = cudaMemcpy2DAsync(work, (size_t)n * sizeof(double), W, (size_t)ldw * sizeof(double),
                              (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return e;
@@ -455,7 +474,10 @@ cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl,
   if ((e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double), (size_t)n, s)) !=
       cudaSuccess)
     return e;
-  return rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s, ws, wsn);
+  if ((e = rec(n, work, n, L, ldl, Y, ldy, U, n, st, pass, 0, s, ws, wsn)) != cudaSuccess) return e;
+  if (Rt != nullptr && (e = transpose_lower(L, ldl, n, Rt, ldrt, s)) != cudaSuccess) return e;
+  if (Rp != nullptr) return pack_rinv_from_lower(Y, ldy, n, Rp, s);
+  return cudaSuccess;
 }
 
 // Shift of the shifted CholeskyQR pass: W += s I with

@@ -38,7 +38,8 @@ cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double*
 // ---------------------------------------------------------------- Q-form
 // Q = A Rinv for upper-triangular Rinv (Algorithm CQR step 3).
 // Small-n path (n <= 256): one row per lane, warps own column groups.
-int qform_group_width(int n);  // columns per group (16 groups), 0 if n > 256
+int qform_group_width(int n);  // columns per group (RP_GROUPS groups), 0 if n > 256
+constexpr int RP_GROUPS = 16;  // column groups of the packed R^-1
 size_t rpack_doubles(int n);
 // Rp[g][k][c] = Rinv(k, g*w + c) for k <= g*w + c, else 0; Rinv = Y^T.
 cudaError_t pack_rinv_from_lower(const double* Y, int64_t ldy, int n, double* Rp, cudaStream_t s);
@@ -86,9 +87,12 @@ cudaError_t trmm_upper_small(int n, const double* A, int64_t lda, bool a_trans, 
 constexpr int CHOLINV_BASE = 64;
 // ws (wsn doubles, may be null) is split-k scratch for the recursion's small
 // products; cholinv_splitk_doubles() is enough for any n.
+// With Rt, also R = L^T (ld ldrt, zeros below the diagonal); with Rp, also
+// the Q-form's packed R^-1 (pack_rinv_from_lower). At n = 64 one kernel writes
+// everything; otherwise the transpose and the packing are launches of their own.
 cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl, double* Y, int64_t ldy,
                     double* work, double* U, DevStatus* st, int pass, cudaStream_t s, double* ws = nullptr,
-                    size_t wsn = 0);
+                    size_t wsn = 0, double* Rt = nullptr, int64_t ldrt = 0, double* Rp = nullptr);
 size_t cholinv_splitk_doubles();
 // Inverse depth (the paper's triangular inverted blocks): the top `depth`
 // halvings form L21 = W21 L11^-T by block forward substitution and leave Y21
