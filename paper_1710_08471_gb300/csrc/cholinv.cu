@@ -461,6 +461,8 @@ cudaError_t cholinv(int n, const double* W, int64_t ldw, double* L, int64_t ldl,
   if (n == NB) {
     // one base case: straight from W, with R and the packed R^-1 when asked
     const int rpw = Rp != nullptr ? qform_group_width(n) : 0;
+    // the packing's layout is the Q-form's: the same number of column groups
+    if (Rp != nullptr && rpack_doubles(n) != (size_t)RP_GROUPS * n * rpw) return cudaErrorInvalidValue;
     k_cholinv_base64<<<1, 32 * (B64_BW + 1), BASE_SMEM, s>>>(W, ldw, L, ldl, Y, ldy, Rt, ldrt, Rp, rpw, st, pass, 0);
     count_launch();
     return cudaGetLastError();

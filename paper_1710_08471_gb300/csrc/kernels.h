@@ -39,7 +39,7 @@ cudaError_t gram_reduce(const double* partial, const GramGeom& g, int n, double*
 // Q = A Rinv for upper-triangular Rinv (Algorithm CQR step 3).
 // Small-n path (n <= 256): one row per lane, warps own column groups.
 int qform_group_width(int n);  // columns per group (RP_GROUPS groups), 0 if n > 256
-constexpr int RP_GROUPS = 16;  // column groups of the packed R^-1
+constexpr int RP_GROUPS = 16;  // column groups of the packed R^-1 (the Q-form's NGROUP; checked at run time)
 size_t rpack_doubles(int n);
 // Rp[g][k][c] = Rinv(k, g*w + c) for k <= g*w + c, else 0; Rinv = Y^T.
 cudaError_t pack_rinv_from_lower(const double* Y, int64_t ldy, int n, double* Rp, cudaStream_t s);

@@ -19,7 +19,7 @@ namespace cqr2 {
 namespace {
 
 constexpr int PANEL = 32;   // rows per panel (one per lane)
-constexpr int NGROUP = RP_GROUPS;  // column groups
+constexpr int NGROUP = 16;  // column groups
 constexpr int QT = 256;     // threads per CTA
 
 __global__ void k_pack_rinv(const double* __restrict__ X, int64_t ldx, int n, int w, bool from_lower,
