@@ -213,35 +213,44 @@ cudaError_t gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double
 }
 
 // R = op(A) B of two upper-triangular n x n factors (the R2 R1 of Algorithm
-// CQR2), n <= TRMM_SMALL_MAX, in one launch: CTA j forms column j and thread
-// i sums op(A)(i, k) B(k, j) for k = i..j in order; C below the diagonal is
+// CQR2), n <= TRMM_SMALL_MAX, in one launch: CTA j forms column j; four
+// threads share each element, thread q summing op(A)(i, k) B(k, j) over
+// k = i + q, i + q + 4, ... <= j in order, and the four partial sums are
+// added in a fixed order through two shuffles (a chain of at most 32 FMAs
+// where one thread per element would hold 128). C below the diagonal is
 // written as 0. op(A)(i, k) = A(k, i) when a_trans (A holds the lower
 // transpose, as the Cholesky factor L2 does), else A(i, k). The general GEMM
 // needs a split-k launch and its reduction for this 2 n^3 / 6 flop product.
-__global__ void __launch_bounds__(TRMM_SMALL_MAX) k_trmm_upper_small(int n, const double* __restrict__ A, int64_t lda,
-                                                                     bool a_trans, const double* __restrict__ B,
-                                                                     int64_t ldb, double* __restrict__ C, int64_t ldc) {
-  const int j = blockIdx.x, i = threadIdx.x;
-  if (i >= n) return;
+constexpr int TRMM_PARTS = 4;
+__global__ void __launch_bounds__(TRMM_PARTS * TRMM_SMALL_MAX)
+    k_trmm_upper_small(int n, const double* __restrict__ A, int64_t lda, bool a_trans, const double* __restrict__ B,
+                       int64_t ldb, double* __restrict__ C, int64_t ldc) {
+  __shared__ double bj[TRMM_SMALL_MAX];
+  const int j = blockIdx.x, t = threadIdx.x, i = t / TRMM_PARTS, q = t % TRMM_PARTS;
+  for (int k = t; k <= j; k += blockDim.x) bj[k] = B[k + (int64_t)j * ldb];
+  __syncthreads();
   double acc = 0.0;
-  if (i <= j) {
-    const double* b = B + (int64_t)j * ldb;
+  if (i <= j) {  // i < n since j < n
     if (a_trans) {
       const double* a = A + (int64_t)i * lda;  // column i of the lower factor
 #pragma unroll 4
-      for (int k = i; k <= j; ++k) acc = fma(a[k], b[k], acc);
+      for (int k = i + q; k <= j; k += TRMM_PARTS) acc = fma(a[k], bj[k], acc);
     } else {
 #pragma unroll 4
-      for (int k = i; k <= j; ++k) acc = fma(A[i + (int64_t)k * lda], b[k], acc);
+      for (int k = i + q; k <= j; k += TRMM_PARTS) acc = fma(A[i + (int64_t)k * lda], bj[k], acc);
     }
   }
-  C[i + (int64_t)j * ldc] = acc;
+  // (p0 + p1) + (p2 + p3): the four threads of an element are adjacent lanes
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (q == 0 && i < n) C[i + (int64_t)j * ldc] = acc;
 }
 
 cudaError_t trmm_upper_small(int n, const double* A, int64_t lda, bool a_trans, const double* B, int64_t ldb,
                              double* C, int64_t ldc, cudaStream_t s) {
   if (n < 1 || n > TRMM_SMALL_MAX) return cudaErrorInvalidValue;
-  k_trmm_upper_small<<<n, (n + 31) / 32 * 32, 0, s>>>(n, A, lda, a_trans, B, ldb, C, ldc);
+  const int threads = (TRMM_PARTS * n + 31) / 32 * 32;
+  k_trmm_upper_small<<<n, threads, 0, s>>>(n, A, lda, a_trans, B, ldb, C, ldc);
   count_launch();
   return cudaGetLastError();
 }
