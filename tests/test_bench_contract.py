@@ -58,3 +58,14 @@ def test_reference_arm_batch_workload():
     assert cfg["m"] == 4096 and cfg["n"] == 32 and cfg["count"] == 1024 and cfg["sampled_problems"] == 4
     assert cfg["variant"] == "grouped" and cfg["precision"] == "fp64"
     assert d["cpu_baseline"]["kind"] == "oracle" and "4 of the 1024 problems" in d["cpu_baseline"]["sample"]
+
+
+def test_small_inputs_are_timed_with_l2_flushed():
+    """Inputs that fit in L2 (129 MB) would stay there between timed steps: the
+    config (shared by both arms) says that a larger buffer is rewritten between
+    steps; inputs larger than L2 say that none is."""
+    small = _line("--impl", "reference", "--steps", "1", "--warmup", "1", "--workload", "small")
+    assert "rewritten between steps" in small["config"]["l2"]
+    tall = _line("--impl", "reference", "--steps", "1", "--warmup", "1", "--oracle-rows", "65536",
+                 "--workload", "tall")
+    assert "no flush" in tall["config"]["l2"] and "> 129 MB" in tall["config"]["l2"]
